@@ -1,0 +1,288 @@
+"""Seeded synthetic graph generators (inputs only: no k-clique arithmetic here).
+
+Every generator draws its randomness from SplitMix64 used as a counter-based
+generator (Steele, Lea and Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014): output i of a stream is the SplitMix64 finaliser
+applied to ``key + (i + 1) * 0x9E3779B97F4A7C15``.  A stream key is derived
+from ``(seed, tag)`` the same way, so every draw is a pure function of
+``(seed, tag, counter)`` and does not depend on numpy's generator versions.
+
+The graphs stand in for the paper's SNAP workloads (Section 4.1): they are
+symmetrised, stripped of self-loops and duplicate edges and returned as a u32
+CSR ``(row_ptr[n+1], col_idx[nnz])`` with every row sorted ascending.
+
+Both the CUDA path's tests/bench and the CPU oracle's tests consume these
+graphs; nothing in this module counts, orients or intersects anything.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+_MASK64 = (1 << 64) - 1
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    """SplitMix64 finaliser on a uint64 array (wrapping arithmetic)."""
+    z = z.astype(np.uint64, copy=True)
+    with np.errstate(over="ignore"):
+        z ^= z >> np.uint64(30)
+        z *= _M1
+        z ^= z >> np.uint64(27)
+        z *= _M2
+        z ^= z >> np.uint64(31)
+    return z
+
+
+def stream_key(seed: int, tag: int) -> int:
+    """64-bit key of the stream named ``tag`` under ``seed``."""
+    x = np.array([((seed & 0xFFFFFFFF) << 24 | (tag & 0xFFFFFF)) & _MASK64], dtype=np.uint64)
+    return int(_mix(x)[0])
+
+
+def random_u64(key: int, counters: np.ndarray) -> np.ndarray:
+    """Outputs ``counters`` (uint64 array) of the stream with 64-bit ``key``."""
+    c = np.asarray(counters, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(key) + (c + np.uint64(1)) * _GOLDEN
+    return _mix(z)
+
+
+def uniform(key: int, counters: np.ndarray) -> np.ndarray:
+    """Doubles in [0, 1) from the top 53 bits of ``random_u64``."""
+    return (random_u64(key, counters) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+# ----------------------------------------------------------------------------
+# CSR assembly
+# ----------------------------------------------------------------------------
+
+@dataclass
+class CSRGraph:
+    """Simple undirected graph as a symmetric u32 CSR with sorted rows."""
+
+    n: int
+    row_ptr: np.ndarray  # uint32[n+1]
+    col_idx: np.ndarray  # uint32[nnz], nnz = 2 * num_edges
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    @property
+    def num_edges(self) -> int:
+        return self.nnz // 2
+
+    def degrees(self) -> np.ndarray:
+        return np.diff(self.row_ptr.astype(np.int64))
+
+    def edge_pairs(self) -> tuple[np.ndarray, np.ndarray]:
+        """Each undirected edge once, as (lo, hi) with lo < hi."""
+        src = np.repeat(np.arange(self.n, dtype=np.int64), self.degrees())
+        dst = self.col_idx.astype(np.int64)
+        keep = src < dst
+        return src[keep], dst[keep]
+
+
+def edges_to_csr(n: int, u: np.ndarray, v: np.ndarray, name: str = "") -> CSRGraph:
+    """Symmetrise, drop self-loops and duplicates, sort rows; return the CSR."""
+    u = np.asarray(u, dtype=np.int64)
+    v = np.asarray(v, dtype=np.int64)
+    if u.size and (u.min() < 0 or v.min() < 0 or u.max() >= n or v.max() >= n):
+        raise ValueError("edge endpoint out of range")
+    keep = u != v
+    lo = np.minimum(u[keep], v[keep]).astype(np.uint64)
+    hi = np.maximum(u[keep], v[keep]).astype(np.uint64)
+    key = np.unique(lo * np.uint64(n) + hi)
+    lo = (key // np.uint64(n)).astype(np.int64)
+    hi = (key % np.uint64(n)).astype(np.int64)
+    src = np.concatenate([lo, hi])
+    dst = np.concatenate([hi, lo])
+    order = np.argsort(src.astype(np.uint64) * np.uint64(n) + dst.astype(np.uint64), kind="stable")
+    src = src[order]
+    dst = dst[order]
+    if dst.size >= (1 << 32):
+        raise ValueError("nnz does not fit in u32")
+    counts = np.bincount(src, minlength=n)
+    row_ptr = np.zeros(n + 1, dtype=np.uint32)
+    np.cumsum(counts, out=row_ptr[1:])
+    return CSRGraph(n=n, row_ptr=row_ptr, col_idx=dst.astype(np.uint32), name=name)
+
+
+def disjoint_union(graphs: list[CSRGraph], name: str = "") -> CSRGraph:
+    """Vertex-disjoint union; vertex ids of graph i are shifted by the sizes before it."""
+    us, vs, off = [], [], 0
+    for g in graphs:
+        a, b = g.edge_pairs()
+        us.append(a + off)
+        vs.append(b + off)
+        off += g.n
+    return edges_to_csr(off, np.concatenate(us) if us else np.zeros(0), np.concatenate(vs) if vs else np.zeros(0), name)
+
+
+def relabel(g: CSRGraph, perm: np.ndarray, name: str = "") -> CSRGraph:
+    """The same graph with vertex v renamed perm[v]."""
+    a, b = g.edge_pairs()
+    perm = np.asarray(perm, dtype=np.int64)
+    return edges_to_csr(g.n, perm[a], perm[b], name or g.name)
+
+
+def random_permutation(n: int, seed: int, tag: int = 0x5E) -> np.ndarray:
+    """A seeded permutation of range(n) (sort by random keys)."""
+    keys = random_u64(stream_key(seed, tag), np.arange(n, dtype=np.uint64))
+    return np.argsort(keys, kind="stable").astype(np.int64)
+
+
+# ----------------------------------------------------------------------------
+# Deterministic families with known clique counts (used as test inputs)
+# ----------------------------------------------------------------------------
+
+def complete_graph(n: int) -> CSRGraph:
+    i, j = np.triu_indices(n, 1)
+    return edges_to_csr(n, i, j, f"K{n}")
+
+
+def complete_multipartite(parts: list[int]) -> CSRGraph:
+    """K_{a1,...,ar}: vertices in different parts are adjacent, same part not."""
+    n = int(sum(parts))
+    label = np.repeat(np.arange(len(parts)), parts)
+    i, j = np.triu_indices(n, 1)
+    keep = label[i] != label[j]
+    return edges_to_csr(n, i[keep], j[keep], "K_" + ",".join(map(str, parts)))
+
+
+def turan_graph(n: int, r: int) -> CSRGraph:
+    """T(n, r): complete r-partite with part sizes as equal as possible."""
+    parts = [n // r + (1 if i < n % r else 0) for i in range(r)]
+    g = complete_multipartite([p for p in parts if p > 0])
+    g.name = f"T({n},{r})"
+    return g
+
+
+def join(g: CSRGraph, h: CSRGraph) -> CSRGraph:
+    """G join H: disjoint union plus every edge between V(G) and V(H)."""
+    a, b = g.edge_pairs()
+    c, d = h.edge_pairs()
+    x, y = np.meshgrid(np.arange(g.n), np.arange(h.n) + g.n, indexing="ij")
+    u = np.concatenate([a, c + g.n, x.ravel()])
+    v = np.concatenate([b, d + g.n, y.ravel()])
+    return edges_to_csr(g.n + h.n, u, v, f"({g.name})v({h.name})")
+
+
+def cycle_graph(n: int) -> CSRGraph:
+    i = np.arange(n)
+    return edges_to_csr(n, i, (i + 1) % n, f"C{n}")
+
+
+def random_tree(n: int, seed: int) -> CSRGraph:
+    """Vertex i > 0 attaches to a uniformly drawn earlier vertex."""
+    if n <= 1:
+        return edges_to_csr(n, np.zeros(0), np.zeros(0), f"tree{n}")
+    i = np.arange(1, n, dtype=np.int64)
+    par = np.floor(uniform(stream_key(seed, 0x7E), i.astype(np.uint64)) * i).astype(np.int64)
+    return edges_to_csr(n, i, par, f"tree{n}")
+
+
+def random_bipartite(a: int, b: int, p: float, seed: int) -> CSRGraph:
+    i, j = np.meshgrid(np.arange(a), np.arange(b) + a, indexing="ij")
+    i, j = i.ravel(), j.ravel()
+    keep = uniform(stream_key(seed, 0xB1), np.arange(i.size, dtype=np.uint64)) < p
+    return edges_to_csr(a + b, i[keep], j[keep], f"bip({a},{b},{p})")
+
+
+def dense_random_graph(n: int, p: float, seed: int) -> CSRGraph:
+    """G(n, p) by one Bernoulli draw per pair (for small n)."""
+    i, j = np.triu_indices(n, 1)
+    keep = uniform(stream_key(seed, 0xD5), np.arange(i.size, dtype=np.uint64)) < p
+    return edges_to_csr(n, i[keep], j[keep], f"G({n},{p})s{seed}")
+
+
+# ----------------------------------------------------------------------------
+# Erdos-Renyi G(n, p) by geometric skipping (Batagelj and Brandes, 2005)
+# ----------------------------------------------------------------------------
+
+def _pair_from_linear(n: int, L: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Map a linear index over pairs i<j (row-major) to (i, j)."""
+    L = L.astype(np.int64)
+    b = 2 * n - 1
+    i = np.floor((b - np.sqrt(np.maximum(b * b - 8.0 * L, 0.0))) / 2).astype(np.int64)
+    i = np.clip(i, 0, n - 2)
+    off = i * (2 * n - i - 1) // 2
+    # fix rounding: make off(i) <= L < off(i+1)
+    for _ in range(3):
+        too_big = off > L
+        i = np.where(too_big, i - 1, i)
+        off = i * (2 * n - i - 1) // 2
+        nxt = (i + 1) * (2 * n - i - 2) // 2
+        too_small = L >= nxt
+        i = np.where(too_small, i + 1, i)
+        off = i * (2 * n - i - 1) // 2
+    j = L - off + i + 1
+    return i, j
+
+
+def erdos_renyi(n: int, p: float, seed: int = 0) -> CSRGraph:
+    """G(n, p): each of the n(n-1)/2 pairs is an edge independently with prob p.
+
+    Gaps between successive edges in the row-major pair order are geometric;
+    the k-th gap is drawn from counter k of the stream (seed, 0xE5).
+    """
+    N = n * (n - 1) // 2
+    if p <= 0 or N == 0:
+        return edges_to_csr(n, np.zeros(0), np.zeros(0), f"ER({n},{p})")
+    if p >= 1:
+        return complete_graph(n)
+    key = stream_key(seed, 0xE5)
+    logq = math.log1p(-p)
+    pos_all = []
+    last = -1
+    drawn = 0
+    batch = int(N * p * 1.05) + 1024
+    while True:
+        u = uniform(key, np.arange(drawn, drawn + batch, dtype=np.uint64))
+        drawn += batch
+        gaps = np.floor(np.log1p(-u) / logq).astype(np.int64)
+        pos = last + np.cumsum(gaps + 1)
+        inside = pos < N
+        pos_all.append(pos[inside])
+        if not inside.all():
+            break
+        last = int(pos[-1])
+    L = np.concatenate(pos_all)
+    i, j = _pair_from_linear(n, L)
+    return edges_to_csr(n, i, j, f"ER({n},{p})s{seed}")
+
+
+# ----------------------------------------------------------------------------
+# R-MAT (Chakrabarti, Zhan and Faloutsos, SDM 2004)
+# ----------------------------------------------------------------------------
+
+def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+         seed: int = 0) -> CSRGraph:
+    """R-MAT with 2**scale vertices and edge_factor * 2**scale generated edges.
+
+    Edge e descends ``scale`` levels; at level l the quadrant is chosen by
+    counter ``e * scale + l`` of the stream (seed, 0xA7), most significant bit
+    first.  No noise and no vertex permutation; the result is symmetrised and
+    deduplicated by ``edges_to_csr``.
+    """
+    n = 1 << scale
+    m = edge_factor * n
+    key = stream_key(seed, 0xA7)
+    src = np.zeros(m, dtype=np.int64)
+    dst = np.zeros(m, dtype=np.int64)
+    base = np.arange(m, dtype=np.uint64) * np.uint64(scale)
+    ab, abc = a + b, a + b + c
+    for lvl in range(scale):
+        u = uniform(key, base + np.uint64(lvl))
+        bit_s = (u >= ab).astype(np.int64)
+        bit_d = (((u >= a) & (u < ab)) | (u >= abc)).astype(np.int64)
+        src = (src << 1) | bit_s
+        dst = (dst << 1) | bit_d
+    return edges_to_csr(n, src, dst, f"RMAT{scale}-ef{edge_factor}s{seed}")

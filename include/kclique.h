@@ -1,0 +1,179 @@
+/*
+ * kclique.h -- exact k-clique counting on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is that of "Parallel K-clique Counting on GPUs" (Almasri,
+ * El Hajj, Nagi, Xiong, Hwu; ICS '22):
+ *   - the undirected graph is oriented into a DAG by degree or degeneracy
+ *     order (Section 3.1);
+ *   - every root vertex (vertex-centric) or root edge (edge-centric) gets the
+ *     binary-encoded sub-graph induced by its out-neighbours (Sections 2.4,
+ *     3.2 and 3.4);
+ *   - a depth-first search with an explicit stack does a bitwise AND plus
+ *     popcount per tree node (Fig. 2, Section 3.3), or, in pivoting mode,
+ *     selects a pivot per node and counts every clique size at once (Fig. 3);
+ *   - counts are reduced into exact 128-bit totals on the device and
+ *     reported as uint64 plus an overflow flag.
+ *
+ * Conventions for every call:
+ *   - Every function returns a kc_status code (KC_OK = 0).  No function
+ *     aborts, exits or traps.  kc_last_error() gives a message for the last
+ *     failing call on the calling host thread.
+ *   - Vertex ids are uint32, counts uint64.  A graph is a CSR: row_ptr[n+1]
+ *     (row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz) and col_idx[nnz].
+ *     nnz must be below 2^32.  The graph must be simple and undirected:
+ *     symmetric, no self-loops, no duplicate entries, every row strictly
+ *     ascending, every id < n.  A violation gives KC_E_INVALID_GRAPH.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is enqueued on it in order.  Calls that return values in
+ *     host memory synchronise that stream before returning.
+ *   - The caller owns every array it passes; the library copies what it keeps.
+ *   - A graph handle may be used by one host thread at a time.
+ */
+#ifndef KCLIQUE_H
+#define KCLIQUE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+typedef int kc_status;
+#define KC_OK 0
+#define KC_E_INVALID_ARG 1     /* a bad argument (null pointer, k = 0, unknown enum, ...) */
+#define KC_E_INVALID_GRAPH 2   /* the CSR is not a simple undirected graph */
+#define KC_E_NO_MEMORY 3       /* a device or host allocation failed */
+#define KC_E_OVERFLOW 4        /* a count exceeded 2^64 - 1; outputs are still written, see flags */
+#define KC_E_TIMEOUT 5         /* a bounded device wait gave up; results are not valid */
+#define KC_E_CUDA 6            /* a CUDA runtime call failed */
+#define KC_E_INTERNAL 7        /* a device-side consistency check failed */
+#define KC_E_UNSUPPORTED 8     /* a size beyond what this build handles */
+
+/* ---- enumerations ------------------------------------------------------ */
+/* Orientation criterion (Section 3.1). */
+#define KC_ORIENT_DEGREE 0      /* u -> v iff (deg u, u) < (deg v, v) */
+#define KC_ORIENT_DEGENERACY 1  /* u -> v iff (peel round u, u) < (peel round v, v) */
+
+/* Parallelisation scheme (Section 3.2). */
+#define KC_SCHEME_AUTO 0        /* vertex-centric for k < 6, edge-centric otherwise (Section 4.5) */
+#define KC_SCHEME_VC 1          /* one root vertex per work item */
+#define KC_SCHEME_EC 2          /* one root edge per work item */
+
+/* Result flag bits. */
+#define KC_FLAG_TOTAL_OVERFLOW 1u       /* the total exceeded 2^64 - 1 */
+#define KC_FLAG_VERTEX_OVERFLOW 2u      /* some per-vertex count exceeded 2^64 - 1 */
+#define KC_FLAG_TIMEOUT 4u              /* a device wait ran out of time */
+#define KC_FLAG_INTERNAL 8u             /* a device-side check failed */
+
+typedef struct kc_graph kc_graph;
+
+typedef struct kc_graph_info {
+    uint32_t n;            /* vertices */
+    uint32_t d_max;        /* maximum out-degree of the DAG */
+    uint64_t num_edges;    /* undirected edges (= DAG edges) */
+    uint32_t degeneracy;   /* max core number (degeneracy orientation), else 0xFFFFFFFF */
+    int32_t orient;        /* KC_ORIENT_* */
+    uint64_t device_bytes; /* device memory held by the handle */
+    float orient_ms;       /* device time of the orientation kernels */
+} kc_graph_info;
+
+/* Result written to DEVICE memory by the asynchronous calls. */
+typedef struct kc_result {
+    uint64_t total;        /* low 64 bits of the exact count */
+    uint64_t total_hi;     /* high 64 bits (non-zero iff the count overflowed uint64) */
+    uint32_t flags;        /* KC_FLAG_* */
+    uint32_t status;       /* KC_OK or the kc_status of a device-side failure */
+} kc_result;
+
+/* ---- errors -------------------------------------------------------------- */
+/* Message for the last failing call on this host thread ("" if none).  The
+ * pointer stays valid until the next library call on this thread. */
+const char* kc_last_error(void);
+/* Static name of a status code ("KC_OK", ...). */
+const char* kc_status_name(kc_status s);
+/* Library version, major * 10000 + minor * 100 + patch. */
+int kc_version(void);
+
+/* ---- graphs ---------------------------------------------------------------- */
+/* Build a resident, oriented graph (Section 3.1: orientation on the device,
+ * undesired directions dropped, row pointers rebuilt by histogram + scan).
+ *   row_ptr, col_idx: the CSR, in host memory (ptrs_on_device = 0) or device
+ *     memory (ptrs_on_device = 1); read during the call only.
+ *   orient: KC_ORIENT_DEGREE or KC_ORIENT_DEGENERACY.
+ *   validate: 1 = check that the CSR is simple and undirected (one pass on the
+ *     device); 0 = trust the caller (results are undefined on a bad graph).
+ *   out: receives the handle; release it with kc_graph_destroy.
+ * Errors: KC_E_INVALID_ARG, KC_E_INVALID_GRAPH, KC_E_NO_MEMORY, KC_E_CUDA,
+ * KC_E_TIMEOUT (the degeneracy peel's bounded grid barrier gave up). */
+kc_status kc_graph_create(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t nnz,
+                          int ptrs_on_device, int orient, int validate, void* stream, kc_graph** out);
+
+/* Free the handle and its device memory.  NULL is accepted. */
+kc_status kc_graph_destroy(kc_graph* g);
+
+kc_status kc_graph_info_get(const kc_graph* g, kc_graph_info* out);
+
+/* Copy the oriented graph to host memory (for inspection and tests).
+ *   dag_row_ptr[n+1], dag_col[num_edges]: the DAG in the library's vertex
+ *     numbering, where vertex r is the r-th vertex of the orientation order,
+ *     so every edge goes from a smaller to a larger id and rows ascend;
+ *   new_of_old[n]: the library id of each input vertex;
+ *   core[n]: core numbers (degeneracy orientation only; otherwise pass NULL).
+ * Any pointer may be NULL to skip that array. */
+kc_status kc_graph_export(const kc_graph* g, uint32_t* dag_row_ptr, uint32_t* dag_col, uint32_t* new_of_old,
+                          uint32_t* core);
+
+/* ---- counting ------------------------------------------------------------- */
+/* Exact number of k-cliques (Sections 2.2-2.4, 3.2-3.6).
+ *   k >= 1 (k = 1 gives n, k = 2 the edge count, both without a launch).
+ *   pivot: 0 = graph-orientation traversal (Fig. 2); 1 = pivoting traversal
+ *     restricted to size k (Fig. 3, stopping when more than k vertices are
+ *     held).
+ *   scheme: KC_SCHEME_AUTO / VC / EC.
+ *   subwarp: threads per group for the big-subgraph path, 0 = automatic,
+ *     else 1, 2, 4, 8, 16 or 32 (Section 3.5).
+ *   total_out (host): the count modulo 2^64.
+ *   per_vertex_out (nullable, n entries, host or device memory): c_k(v), the
+ *     number of k-cliques containing input vertex v, modulo 2^64.
+ *   flags_out (nullable, host): KC_FLAG_* bits.
+ * Returns KC_E_OVERFLOW (with every output written) when the total or a
+ * per-vertex count exceeded 2^64 - 1. */
+kc_status kc_count(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_t subwarp, uint64_t* total_out,
+                   uint64_t* per_vertex_out, uint32_t* flags_out, void* stream);
+
+/* Same count with both 64-bit words of the exact value (the count is exact
+ * below 2^128; flags as above). */
+kc_status kc_count128(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_t subwarp, uint64_t* lo_out,
+                      uint64_t* hi_out, uint32_t* flags_out, void* stream);
+
+/* Asynchronous form: enqueue the count on `stream` and return.  The result is
+ * written to result_dev (device memory) when the stream reaches it.  Device
+ * working memory is taken from the handle; call kc_graph_reserve first if the
+ * call will be captured into a CUDA graph (no allocation happens then).
+ * per_vertex_dev: nullable, n entries of device memory, input numbering. */
+kc_status kc_count_async(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_t subwarp, kc_result* result_dev,
+                         uint64_t* per_vertex_dev, void* stream);
+
+/* Pre-allocate the device working memory kc_count_async will need for these
+ * parameters (pivot as in kc_count; k_max = the largest k to be asked). */
+kc_status kc_graph_reserve(kc_graph* g, uint32_t k_max, int pivot, int per_vertex, void* stream);
+
+/* Every clique size at once by pivoting (Fig. 3, Section 2.3).
+ *   counts (host, cap entries): counts[j] = number of j-cliques modulo 2^64,
+ *     counts[0] = 1 by convention, entries beyond the clique number are 0.
+ *   overflow (host, nullable, cap entries): 1 where counts[j] exceeded 2^64-1.
+ *   omega_out (nullable): the clique number.
+ *   per_vertex_k, per_vertex_out: if per_vertex_k > 0 and per_vertex_out is
+ *     not NULL, per_vertex_out[v] = c_{per_vertex_k}(v) modulo 2^64 (n entries,
+ *     host or device memory).
+ * Returns KC_E_OVERFLOW (outputs written) when any reported count overflowed. */
+kc_status kc_count_all(kc_graph* g, uint64_t* counts, uint8_t* overflow, uint32_t cap, uint32_t* omega_out,
+                       uint32_t per_vertex_k, uint64_t* per_vertex_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KCLIQUE_H */

@@ -1,0 +1,208 @@
+// Internal declarations shared by the CUDA translation units of libkclique.
+// Nothing here is part of the public C ABI (include/kclique.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "kclique.h"
+
+#define KC_VERSION 10000
+
+// ---------------------------------------------------------------------------
+// Host-side error plumbing
+// ---------------------------------------------------------------------------
+namespace kc {
+
+kc_status set_error(kc_status s, const char* fmt, ...);
+void clear_error();
+kc_status cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+}  // namespace kc
+
+#define KC_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return kc::cuda_error(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define KC_CHECK(st)                      \
+    do {                                  \
+        kc_status s_ = (st);              \
+        if (s_ != KC_OK) return s_;       \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Device buffers owned by a handle
+// ---------------------------------------------------------------------------
+namespace kc {
+
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+kc_status dev_alloc(DevBuf& b, size_t bytes);      // (re)allocate if smaller than `bytes`
+void dev_free(DevBuf& b);
+
+// Per-launch error word written by kernels (device) -- bit layout = KC_FLAG_*.
+struct Ctl {
+    unsigned long long total_lo;   // exact 128-bit count, low word
+    unsigned long long total_hi;   // carries out of total_lo
+    unsigned int flags;            // KC_FLAG_* bits
+    unsigned int work_next;        // big-root work counter
+    unsigned int work_next_small;  // small-root work counter
+    unsigned int work_next_aux;    // spare counter
+    unsigned int bar_count;        // grid barrier arrivals
+    unsigned int bar_gen;          // grid barrier generation
+};
+
+}  // namespace kc
+
+// The opaque handle of the public API.
+struct kc_graph {
+    uint32_t n = 0;
+    uint64_t m = 0;             // undirected edges == DAG edges
+    uint32_t d_max = 0;         // max DAG out-degree
+    uint32_t degeneracy = 0xFFFFFFFFu;
+    int orient = 0;
+    float orient_ms = 0.f;
+    int device = 0;
+    int sm_count = 0;
+    // DAG in the library numbering (vertex r = r-th vertex of the order)
+    kc::DevBuf row_ptr;      // u32[n+1]
+    kc::DevBuf col;          // u32[m]
+    kc::DevBuf new_of_old;   // u32[n]
+    kc::DevBuf old_of_new;   // u32[n]
+    kc::DevBuf core;         // u32[n] (input numbering), degeneracy only
+    kc::DevBuf roots;        // u32[n] library ids sorted by out-degree, descending
+    kc::DevBuf edge_src;     // u32[m] source of every DAG edge (EC roots), built on first use
+    kc::DevBuf edge_order;   // u32[m] DAG edge ids in work order (EC)
+    std::vector<uint64_t> outdeg_hist;  // host: number of vertices per out-degree (d_max + 1 entries)
+    // working memory for counting
+    kc::DevBuf ctl;          // kc::Ctl
+    kc::DevBuf scratch;      // per-block scratch (global-memory bitmaps and stacks)
+    kc::DevBuf pv;           // u64 per-vertex accumulators (library numbering) + overflow words
+    kc::DevBuf tmp;          // misc temporaries
+    uint64_t device_bytes() const;
+};
+
+// ---------------------------------------------------------------------------
+// Cross-unit entry points (host side)
+// ---------------------------------------------------------------------------
+namespace kc {
+
+// kc_scan.cu: exclusive scan of n u32 values into out (n+1 entries, out[n] =
+// total).  `tmp` is grown as needed.  Returns an error status on CUDA failure.
+kc_status scan_u32(const uint32_t* in, uint32_t* out, size_t n, DevBuf& tmp, cudaStream_t s);
+size_t scan_tmp_bytes(size_t n);
+// Same, with caller-provided scratch of scan_tmp_bytes(n) bytes.
+kc_status scan_u32_raw(const uint32_t* in, uint32_t* out, size_t n, void* tmp, cudaStream_t s);
+
+// kc_sort.cu: stable sort of the ids 0..n-1 by key[id] (ascending; equal keys
+// keep id order).  out_ids receives the sorted ids.  max_key bounds the keys.
+kc_status sort_ids_by_key(const uint32_t* key, uint32_t n, uint32_t max_key, uint32_t* out_ids, DevBuf& tmp,
+                          cudaStream_t s);
+
+// kc_orient.cu
+kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, int validate, cudaStream_t s);
+kc_status ensure_edge_src(kc_graph* g, cudaStream_t s);
+
+// kc_count.cu
+struct CountArgs {
+    uint32_t k;
+    int scheme;       // KC_SCHEME_VC / EC (resolved)
+    uint32_t subwarp; // resolved group width
+    int pivot;
+    uint64_t* per_vertex_dev;  // input numbering, may be null
+};
+kc_status count_launch(kc_graph* g, const CountArgs& a, kc_result* result_dev, cudaStream_t s);
+kc_status count_reserve(kc_graph* g, uint32_t k_max, int pivot, int per_vertex, cudaStream_t s);
+
+// kc_pivot.cu
+kc_status count_all_launch(kc_graph* g, uint32_t cap, uint32_t per_vertex_k, uint64_t* per_vertex_dev,
+                           unsigned long long* counts_dev /* 2*cap words: lo,hi per size */, unsigned int* omega_dev,
+                           unsigned int* flags_dev, cudaStream_t s);
+
+int sm_count_of_current_device();
+
+}  // namespace kc
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace kc {
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned r;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Exact 128-bit accumulation of a 64-bit partial into (lo, hi).
+__device__ __forceinline__ void add_u128(unsigned long long* lo, unsigned long long* hi, unsigned long long x) {
+    if (x == 0) return;
+    unsigned long long old = atomicAdd(lo, x);
+    if (old + x < old) atomicAdd(hi, 1ull);
+}
+
+// Grid-wide barrier for cooperative launches, with a bounded wait: after
+// `limit_ns` of waiting the block records KC_FLAG_TIMEOUT in *flags and
+// returns false (every later barrier then returns false at once).  When dbg
+// is not null a timed-out block records {block, its barrier sequence number,
+// arrivals seen, generation seen, the generation it waited on} there.
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen, unsigned int nblocks,
+                                             unsigned int* flags, unsigned long long limit_ns,
+                                             unsigned int* dbg = nullptr, unsigned int seq = 0) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = (atomicAdd(flags, 0u) & KC_FLAG_TIMEOUT) == 0;
+        if (ok) {
+            unsigned int g = atomicAdd(gen, 0u);
+            __threadfence();
+            if (atomicAdd(count, 1u) == nblocks - 1) {
+                atomicExch(count, 0u);
+                __threadfence();
+                atomicAdd(gen, 1u);
+            } else {
+                unsigned long long t0 = globaltimer_ns();
+                unsigned int spins = 0;
+                while (atomicAdd(gen, 0u) == g) {
+                    __nanosleep(64);
+                    if ((++spins & 255u) == 0 && globaltimer_ns() - t0 > limit_ns) {
+                        if (atomicOr(flags, (unsigned)KC_FLAG_TIMEOUT) == 0u || true) {
+                            if (dbg && atomicCAS(&dbg[0], 0u, 1u) == 0u) {
+                                dbg[1] = blockIdx.x;
+                                dbg[2] = seq;
+                                dbg[3] = atomicAdd(count, 0u);
+                                dbg[4] = atomicAdd(gen, 0u);
+                                dbg[5] = g;
+                                dbg[6] = (unsigned)(globaltimer_ns() - t0);
+                            }
+                        }
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+            __threadfence();
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+}  // namespace kc
+#endif

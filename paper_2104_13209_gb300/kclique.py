@@ -1,0 +1,241 @@
+"""Thin Python binding of libkclique (include/kclique.h).
+
+Argument marshalling only: every step of the counting path runs inside the
+CUDA library.  Host arrays are numpy arrays; device arrays may be given as
+torch CUDA tensors (their data pointers are passed straight through).  The
+library must have been built (``paper_2104_13209_gb300.build.build()``);
+importing this module on a machine without it raises at first use -- there
+is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+KC_OK = 0
+KC_E_INVALID_ARG = 1
+KC_E_INVALID_GRAPH = 2
+KC_E_NO_MEMORY = 3
+KC_E_OVERFLOW = 4
+KC_E_TIMEOUT = 5
+KC_E_CUDA = 6
+KC_E_INTERNAL = 7
+KC_E_UNSUPPORTED = 8
+
+KC_ORIENT_DEGREE = 0
+KC_ORIENT_DEGENERACY = 1
+KC_SCHEME_AUTO = 0
+KC_SCHEME_VC = 1
+KC_SCHEME_EC = 2
+
+KC_FLAG_TOTAL_OVERFLOW = 1
+KC_FLAG_VERTEX_OVERFLOW = 2
+KC_FLAG_TIMEOUT = 4
+KC_FLAG_INTERNAL = 8
+
+_ORIENT = {"degree": KC_ORIENT_DEGREE, "degeneracy": KC_ORIENT_DEGENERACY}
+_SCHEME = {"auto": KC_SCHEME_AUTO, "vc": KC_SCHEME_VC, "ec": KC_SCHEME_EC}
+
+# Every exported symbol of include/kclique.h.
+EXPORTED = [
+    "kc_last_error", "kc_status_name", "kc_version", "kc_graph_create", "kc_graph_destroy", "kc_graph_info_get",
+    "kc_graph_export", "kc_count", "kc_count128", "kc_count_async", "kc_graph_reserve", "kc_count_all",
+]
+
+
+class kc_graph_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("d_max", ctypes.c_uint32), ("num_edges", ctypes.c_uint64),
+                ("degeneracy", ctypes.c_uint32), ("orient", ctypes.c_int32), ("device_bytes", ctypes.c_uint64),
+                ("orient_ms", ctypes.c_float)]
+
+
+class kc_result(ctypes.Structure):
+    _fields_ = [("total", ctypes.c_uint64), ("total_hi", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+                ("status", ctypes.c_uint32)]
+
+
+RESULT_BYTES = ctypes.sizeof(kc_result)
+
+
+class KCError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{status_name(status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libkclique.so (raising if it is absent and build_if_missing is False)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"libkclique.so is not built ({path}); run paper_2104_13209_gb300.build.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    lib.kc_last_error.restype = ctypes.c_char_p
+    lib.kc_last_error.argtypes = []
+    lib.kc_status_name.restype = ctypes.c_char_p
+    lib.kc_status_name.argtypes = [i32]
+    lib.kc_version.restype = i32
+    lib.kc_graph_create.argtypes = [vp, vp, u32, u64, i32, i32, i32, vp, ctypes.POINTER(vp)]
+    lib.kc_graph_destroy.argtypes = [vp]
+    lib.kc_graph_info_get.argtypes = [vp, ctypes.POINTER(kc_graph_info)]
+    lib.kc_graph_export.argtypes = [vp, vp, vp, vp, vp]
+    lib.kc_count.argtypes = [vp, u32, i32, i32, u32, ctypes.POINTER(u64), vp, ctypes.POINTER(u32), vp]
+    lib.kc_count128.argtypes = [vp, u32, i32, i32, u32, ctypes.POINTER(u64), ctypes.POINTER(u64),
+                                ctypes.POINTER(u32), vp]
+    lib.kc_count_async.argtypes = [vp, u32, i32, i32, u32, vp, vp, vp]
+    lib.kc_graph_reserve.argtypes = [vp, u32, i32, i32, vp]
+    lib.kc_count_all.argtypes = [vp, vp, vp, u32, ctypes.POINTER(u32), u32, vp, vp]
+    for f in ("kc_graph_create", "kc_graph_destroy", "kc_graph_info_get", "kc_graph_export", "kc_count",
+              "kc_count128", "kc_count_async", "kc_graph_reserve", "kc_count_all"):
+        getattr(lib, f).restype = i32
+    _lib = lib
+    return lib
+
+
+def status_name(s: int) -> str:
+    try:
+        return load().kc_status_name(s).decode()
+    except Exception:  # library not loadable: plain number
+        return f"status {s}"
+
+
+def last_error() -> str:
+    return load().kc_last_error().decode()
+
+
+def _check(st: int, allow=(KC_OK,)) -> int:
+    if st not in allow:
+        raise KCError(st, last_error())
+    return st
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr_of(x):
+    """(pointer, keepalive, on_device) of a numpy array or torch tensor."""
+    if x is None:
+        return None, None, False
+    if _is_torch(x):
+        if not x.is_contiguous():
+            x = x.contiguous()
+        return x.data_ptr(), x, x.is_cuda
+    a = np.ascontiguousarray(x)
+    return a.ctypes.data, a, False
+
+
+@dataclass
+class CountResult:
+    total: int            # exact count (both words)
+    flags: int
+    overflow: bool        # exceeded 2^64 - 1
+
+    @property
+    def total_u64(self) -> int:
+        return self.total & ((1 << 64) - 1)
+
+
+class Graph:
+    """A resident, oriented graph (kc_graph_create)."""
+
+    def __init__(self, row_ptr, col_idx, n: int | None = None, orient: str = "degeneracy", validate: bool = True,
+                 stream=None):
+        lib = load()
+        rp, rp_keep, rp_dev = _ptr_of(row_ptr if _is_torch(row_ptr) else np.asarray(row_ptr, dtype=np.uint32))
+        ci, ci_keep, ci_dev = _ptr_of(col_idx if _is_torch(col_idx) else np.asarray(col_idx, dtype=np.uint32))
+        if rp_dev != ci_dev:
+            raise ValueError("row_ptr and col_idx must both be on the host or both on the device")
+        if n is None:
+            n = (rp_keep.numel() if _is_torch(rp_keep) else rp_keep.size) - 1
+        nnz = ci_keep.numel() if _is_torch(ci_keep) else ci_keep.size
+        h = ctypes.c_void_p()
+        _check(lib.kc_graph_create(rp, ci if nnz else None, n, nnz, int(rp_dev), _ORIENT[orient], int(validate),
+                                   _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+        self.n = n
+        self.orient = orient
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().kc_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        i = kc_graph_info()
+        _check(load().kc_graph_info_get(self._h, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in kc_graph_info._fields_}
+
+    def export(self, core: bool = False):
+        """(dag_row_ptr, dag_col, new_of_old, core or None) as numpy arrays."""
+        inf = self.info()
+        n, m = inf["n"], inf["num_edges"]
+        rp = np.zeros(n + 1, dtype=np.uint32)
+        col = np.zeros(max(m, 1), dtype=np.uint32)
+        nof = np.zeros(max(n, 1), dtype=np.uint32)
+        cr = np.zeros(max(n, 1), dtype=np.uint32) if core else None
+        _check(load().kc_graph_export(self._h, rp.ctypes.data, col.ctypes.data, nof.ctypes.data,
+                                      cr.ctypes.data if core else None))
+        return rp, col[:m], nof[:n], (cr[:n] if core else None)
+
+    def count(self, k: int, pivot: bool = False, scheme: str = "auto", subwarp: int = 0, stream=None) -> CountResult:
+        lo, hi, fl = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint32()
+        _check(load().kc_count128(self._h, k, int(pivot), _SCHEME[scheme], subwarp, ctypes.byref(lo), ctypes.byref(hi),
+                                  ctypes.byref(fl), _stream_ptr(stream)), allow=(KC_OK, KC_E_OVERFLOW))
+        total = (hi.value << 64) | lo.value
+        return CountResult(total, fl.value, total >= (1 << 64))
+
+    def count_async(self, k: int, result_dev, pivot: bool = False, scheme: str = "auto", subwarp: int = 0,
+                    stream=None):
+        """Enqueue a count writing a kc_result into result_dev (a CUDA tensor of >= 24 bytes)."""
+        p, _, dev = _ptr_of(result_dev)
+        if not dev:
+            raise ValueError("result_dev must be device memory")
+        _check(load().kc_count_async(self._h, k, int(pivot), _SCHEME[scheme], subwarp, p, None, _stream_ptr(stream)))
+
+    def reserve(self, k_max: int, pivot: bool = False, per_vertex: bool = False, stream=None):
+        _check(load().kc_graph_reserve(self._h, k_max, int(pivot), int(per_vertex), _stream_ptr(stream)))
+
+
+def parse_result(raw: bytes) -> CountResult:
+    r = kc_result.from_buffer_copy(raw[:RESULT_BYTES])
+    if r.status != KC_OK:
+        raise KCError(r.status, "device-side failure")
+    total = (r.total_hi << 64) | r.total
+    return CountResult(total, r.flags, total >= (1 << 64))

@@ -1,0 +1,390 @@
+"""Benchmark of the exact k-clique counter on synthetic workloads.
+
+Default workload: R-MAT scale 20 (1,048,576 vertices, edge factor 16,
+a/b/c/d = .57/.19/.19/.05, seed 0), symmetrised and deduplicated, u32 CSR.
+One step = the whole hot path on that graph: degeneracy orientation on the
+device (kc_graph_create from a device-resident CSR) followed by the counts of
+the plan (default: k = 4, vertex-centric, graph-orientation traversal).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank counts its
+own replica of the workload (weak scaling); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2104_13209_gb300 import synth  # noqa: E402
+
+CACHE = os.path.join(ROOT, "paper_2104_13209_gb300", "_build", "cache")
+PROFILES = os.path.join(ROOT, "profiles")
+L2_FLUSH_BYTES = 512 << 20   # larger than the 129 MB L2
+POPC_PER_SM_CLK = 16         # population count results per SM per clock (CUDA arithmetic throughput table)
+SMS = 152
+SM_MAX_HZ = 2.07e9
+
+
+def workload_graph(scale=20, ef=16, seed=0):
+    os.makedirs(CACHE, exist_ok=True)
+    path = os.path.join(CACHE, f"rmat{scale}_ef{ef}_s{seed}.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return synth.CSRGraph(int(z["n"]), z["row_ptr"], z["col_idx"], f"RMAT{scale}-ef{ef}s{seed}")
+    g = synth.rmat(scale, ef, seed=seed)
+    tmp = path + f".tmp{os.getpid()}.npz"
+    np.savez(tmp, n=g.n, row_ptr=g.row_ptr, col_idx=g.col_idx)
+    os.replace(tmp, path)
+    return g
+
+
+def parse_plan(s: str):
+    """'4vc,7pv' -> [(4, 'vc'), ...]."""
+    out = []
+    for tok in s.split(","):
+        tok = tok.strip()
+        k = int("".join(ch for ch in tok if ch.isdigit()))
+        sch = "".join(ch for ch in tok if ch.isalpha()) or "vc"
+        out.append((k, sch))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline: the oracle, as it stands, on a bounded sample of roots
+# ----------------------------------------------------------------------------
+def oracle_sample_rate(g, k: int, budget_s: float, dag=None, stride: int | None = None):
+    """cliques/s of the oracle's Fig. 2 traversal on a uniform sample of roots
+    (every stride-th root with out-degree >= k - 1; the stride is calibrated to
+    about budget_s of work unless given)."""
+    from oracle import oracle as O
+
+    if dag is None:
+        dag = O.dag_for(g.row_ptr, g.col_idx, "degeneracy")
+    drp, dci = dag[0], dag[1]
+    d = np.diff(drp.astype(np.int64))
+    roots = np.nonzero(d >= k - 1)[0].astype(np.uint32)
+    threads = O.default_threads()
+
+    def run(st):
+        sample = roots[::st]
+        t = time.perf_counter()
+        c = O.count_orient(drp, dci, k, roots=sample, threads=threads).total
+        return c, time.perf_counter() - t, int(sample.size)
+
+    if stride is None:
+        stride = 1 << 14
+        while True:
+            c, dt, ns = run(stride)
+            if dt >= budget_s * 0.25 or stride == 1:
+                break
+            stride = max(1, int(stride * max(dt, 1e-3) / budget_s))
+        if dt < budget_s * 0.5 and stride > 1:
+            stride = max(1, int(stride * dt / budget_s))
+    c, dt, ns = run(stride)
+    return {"count": c, "seconds": dt, "roots": ns, "stride": stride, "threads": threads,
+            "rate": c / dt if dt > 0 else None}
+
+
+def run_reference(a, g, plan, world, rank):
+    """--impl reference: the CPU oracle timed on this host's cores on bounded samples."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+
+    t0 = time.perf_counter()
+    dag = O.dag_for(g.row_ptr, g.col_idx, "degeneracy")
+    orient_s = time.perf_counter() - t0
+    k = plan[0][0]
+    per_step = max(2.0, 60.0 / max(1, a.steps + a.warmup))
+    stride = oracle_sample_rate(g, k, per_step, dag)["stride"]
+    for _ in range(a.warmup):
+        oracle_sample_rate(g, k, per_step, dag, stride)
+    cnt, secs, info = 0, 0.0, None
+    for _ in range(a.steps):
+        info = oracle_sample_rate(g, k, per_step, dag, stride)
+        cnt += info["count"]
+        secs += info["seconds"]
+    value = cnt / secs
+    line = {
+        "impl": "reference", "metric": "k-clique count throughput (cliques/s)", "value": value,
+        "unit": "cliques/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * secs / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": g.name, "n": g.n, "edges": g.num_edges, "k": k, "orientation": "degeneracy",
+                   "traversal": "graph orientation (Fig. 2), CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": "cliques/s", "cores": info["threads"], "kind": "oracle",
+                         "sample": f"every {info['stride']}-th root with out-degree >= {k - 1} "
+                                   f"({info['roots']} roots), orientation {orient_s:.1f}s untimed"},
+        "e2e": {"value": value, "unit": "cliques/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def traffic_record(kernel_src: str):
+    """DRAM bytes per launch from profiles/traffic.json if the kernel source is unchanged."""
+    path = os.path.join(PROFILES, "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    if rec.get("kernel_source_sha256_16") != h:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def run_ours(a, g, plan, world, rank, local_rank):
+    import torch
+
+    from paper_2104_13209_gb300 import build, kclique
+
+    build.build()
+    kclique.load()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    rp_d = torch.from_numpy(g.row_ptr.view(np.int32)).to(dev)
+    ci_d = torch.from_numpy(g.col_idx.view(np.int32)).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    results = torch.zeros((len(plan), kclique.RESULT_BYTES), dtype=torch.uint8, device=dev)
+    n, nnz = g.n, int(g.row_ptr[-1])
+
+    def step(timing):
+        """One pass of the hot path; timing: list to which (label, ms) pairs are appended."""
+        with torch.cuda.stream(stream):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            G = kclique.Graph(rp_d, ci_d, n=n, orient="degeneracy", validate=False, stream=stream)
+            e1.record(stream)
+            evs = [("orient", e0, e1)]
+            for i, (k, sch) in enumerate(plan):
+                c0 = torch.cuda.Event(enable_timing=True)
+                c1 = torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
+                G.count_async(k, results[i], scheme=sch, stream=stream)
+                c1.record(stream)
+                evs.append((f"k{k}{sch}", c0, c1))
+            stream.synchronize()
+            G.close()
+        for lab, x0, x1 in evs:
+            timing.append((lab, x0.elapsed_time(x1)))
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        stream.synchronize()
+
+    for _ in range(a.warmup):
+        step([])
+        flush_l2()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = kclique.launch_count()
+    timings = []
+    with ClockSampler(local_rank) as clk:
+        t_wall0 = time.perf_counter()
+        for _ in range(a.steps):
+            flush_l2()
+            step(timings)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    launches = kclique.launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    res = [kclique.parse_result(bytes(results[i].cpu().numpy())) for i in range(len(plan))]
+    step_ms = sum(ms for _, ms in timings) / a.steps
+    per_label = {}
+    for lab, ms in timings:
+        per_label[lab] = per_label.get(lab, 0.0) + ms / a.steps
+    total_cliques = sum(r.total for r in res)
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+
+    # end to end through the public API from pinned host memory
+    rp_h = torch.from_numpy(g.row_ptr.view(np.int32)).pin_memory()
+    ci_h = torch.from_numpy(g.col_idx.view(np.int32)).pin_memory()
+    rp_np = rp_h.numpy().view(np.uint32)
+    ci_np = ci_h.numpy().view(np.uint32)
+
+    def e2e_step():
+        G = kclique.Graph(rp_np, ci_np, n=n, orient="degeneracy", validate=True, stream=stream)
+        tot = 0
+        for k, sch in plan:
+            tot += G.count(k, scheme=sch, stream=stream).total
+        G.close()
+        return tot
+
+    for _ in range(max(1, a.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_times = []
+    for _ in range(a.steps):
+        flush_l2()
+        t0 = time.perf_counter()
+        tot = e2e_step()
+        e2e_times.append(time.perf_counter() - t0)
+        assert tot == total_cliques, "end-to-end count differs from the device-resident count"
+    e2e_s = float(np.mean(e2e_times))
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # roofline of the dominant kernel (the first count of the plan)
+    k0, s0 = plan[0]
+    lab0 = f"k{k0}{s0}"
+    t_cnt = per_label[lab0] / 1e3
+    words = res[0].words
+    achieved = 2.0 * words / t_cnt / 1e12  # Tops/s: one AND + one POPC per 32-bit word
+    peak = 2.0 * SMS * POPC_PER_SM_CLK * SM_MAX_HZ / 1e12
+    traffic = traffic_record(os.path.join(ROOT, "paper_2104_13209_gb300", "csrc", "kc_count.cu"))
+
+    clocks = clk.summary()
+    value = world * total_cliques / (step_ms / 1e3)
+    line = {
+        "metric": "k-clique count throughput (cliques/s)",
+        "value": value,
+        "unit": "cliques/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": step_ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int64",
+        "data": "synthetic",
+        "config": {
+            "workload": g.name, "n": n, "edges": g.num_edges, "orientation": "degeneracy",
+            "plan": [f"k={k} {sch}" for k, sch in plan], "counts": [str(r.total) for r in res],
+            "step_ms_parts": {k: round(v, 3) for k, v in per_label.items()},
+            "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+            "wall_s_timed_region": t_wall, "parallelism": f"replicas x{world}",
+        },
+        "e2e": {"value": world * total_cliques / e2e_s, "unit": "cliques/s",
+                "h2d_bytes_per_step": 4 * (n + 1) + 4 * nnz,
+                "d2h_bytes_per_step": kclique.RESULT_BYTES * len(plan)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": f"k_count_orient ({lab0})", "words": words,
+                     "peak_note": "derived: 152 SMs x 16 popc/clk x 2.07 GHz x 2 ops (AND+POPC) per word"},
+        "clocks": clocks,
+        "gpu_launches": launches,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cb = oracle_sample_rate(g, k0, a.cpu_budget)
+        line["cpu_baseline"] = {"value": cb["rate"], "unit": "cliques/s", "cores": cb["threads"], "kind": "oracle",
+                                "sample": f"k={k0}: every {cb['stride']}-th root with out-degree >= {k0 - 1} "
+                                          f"({cb['roots']} roots, {cb['seconds']:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plan", default="4vc")
+    ap.add_argument("--scale", type=int, default=20)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    a = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    g = workload_graph(a.scale)
+    plan = parse_plan(a.plan)
+    if a.impl == "reference":
+        run_reference(a, g, plan, world, rank)
+    else:
+        run_ours(a, g, plan, world, rank, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

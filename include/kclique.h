@@ -85,6 +85,7 @@ typedef struct kc_result {
     uint64_t total_hi;     /* high 64 bits (non-zero iff the count overflowed uint64) */
     uint32_t flags;        /* KC_FLAG_* */
     uint32_t status;       /* KC_OK or the kc_status of a device-side failure */
+    uint64_t words;        /* 32-bit bitmap words intersected (AND + popcount) by the traversal */
 } kc_result;
 
 /* ---- errors -------------------------------------------------------------- */
@@ -95,6 +96,9 @@ const char* kc_last_error(void);
 const char* kc_status_name(kc_status s);
 /* Library version, major * 10000 + minor * 100 + patch. */
 int kc_version(void);
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all threads, all devices); for accounting of device work. */
+uint64_t kc_launch_count(void);
 
 /* ---- graphs ---------------------------------------------------------------- */
 /* Build a resident, oriented graph (Section 3.1: orientation on the device,
@@ -114,6 +118,13 @@ kc_status kc_graph_create(const uint32_t* row_ptr, const uint32_t* col_idx, uint
 kc_status kc_graph_destroy(kc_graph* g);
 
 kc_status kc_graph_info_get(const kc_graph* g, kc_graph_info* out);
+
+/* Time budget for the counting calls on this graph: a count still running
+ * after `seconds` stops taking work, sets KC_FLAG_TIMEOUT and returns
+ * KC_E_TIMEOUT (its partial count is not valid).  0 = no limit (the default).
+ * The device checks the budget between work items and every few thousand
+ * tree nodes, so it may be overrun by a fraction of a millisecond. */
+kc_status kc_graph_set_time_limit(kc_graph* g, double seconds);
 
 /* Copy the oriented graph to host memory (for inspection and tests).
  *   dag_row_ptr[n+1], dag_col[num_edges]: the DAG in the library's vertex

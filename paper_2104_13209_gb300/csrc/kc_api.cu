@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <string>
 
@@ -13,6 +14,9 @@
 namespace kc {
 
 static thread_local std::string t_err;
+static std::atomic<unsigned long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 kc_status set_error(kc_status s, const char* fmt, ...) {
     char buf[1024];
@@ -71,7 +75,7 @@ static bool is_device_pointer(const void* p) {
 
 uint64_t kc_graph::device_bytes() const {
     const kc::DevBuf* bufs[] = {&row_ptr, &col, &new_of_old, &old_of_new, &core, &roots, &edge_src,
-                                &edge_order, &ctl, &scratch, &pv, &tmp};
+                                &edge_order, &ctl, &result, &pivot_out, &pv_stage, &scratch, &pv, &tmp};
     uint64_t t = 0;
     for (auto* b : bufs) t += b->bytes;
     return t;
@@ -99,6 +103,8 @@ const char* kc_status_name(kc_status s) {
 }
 
 int kc_version(void) { return KC_VERSION; }
+
+uint64_t kc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 kc_status kc_graph_create(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t nnz,
                           int ptrs_on_device, int orient, int validate, void* stream, kc_graph** out) {
@@ -161,7 +167,7 @@ kc_status kc_graph_create(const uint32_t* row_ptr, const uint32_t* col_idx, uint
 kc_status kc_graph_destroy(kc_graph* g) {
     if (!g) return KC_OK;
     DevBuf* bufs[] = {&g->row_ptr, &g->col, &g->new_of_old, &g->old_of_new, &g->core, &g->roots, &g->edge_src,
-                      &g->edge_order, &g->ctl, &g->scratch, &g->pv, &g->tmp};
+                      &g->edge_order, &g->ctl, &g->result, &g->pivot_out, &g->pv_stage, &g->scratch, &g->pv, &g->tmp};
     for (auto* b : bufs) dev_free(*b);
     delete g;
     return KC_OK;
@@ -177,6 +183,14 @@ kc_status kc_graph_info_get(const kc_graph* g, kc_graph_info* out) {
     out->orient = g->orient;
     out->device_bytes = g->device_bytes();
     out->orient_ms = g->orient_ms;
+    return KC_OK;
+}
+
+kc_status kc_graph_set_time_limit(kc_graph* g, double seconds) {
+    clear_error();
+    if (!g) return set_error(KC_E_INVALID_ARG, "NULL graph");
+    if (!(seconds >= 0.0)) return set_error(KC_E_INVALID_ARG, "time limit must be >= 0");
+    g->time_limit_s = seconds;
     return KC_OK;
 }
 
@@ -223,8 +237,11 @@ kc_status kc_count_async(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_
     CountArgs a;
     KC_CHECK(resolve(g, k, pivot, scheme, subwarp, a));
     if (!result_dev) return set_error(KC_E_INVALID_ARG, "result_dev is NULL");
-    if (per_vertex_dev) return set_error(KC_E_UNSUPPORTED, "per-vertex counts are available from kc_count_all");
-    if (pivot) return set_error(KC_E_UNSUPPORTED, "fixed-k pivoting is not built into this library version");
+    if (per_vertex_dev && !is_device_pointer(per_vertex_dev))
+        return set_error(KC_E_INVALID_ARG, "per_vertex_dev must be device memory");
+    if (pivot) return count_pivot_async(g, k, result_dev, per_vertex_dev, (cudaStream_t)stream);
+    if (per_vertex_dev)
+        return set_error(KC_E_UNSUPPORTED, "per-vertex counts come from the pivoting traversal (pivot = 1)");
     return count_launch(g, a, result_dev, (cudaStream_t)stream);
 }
 
@@ -234,44 +251,87 @@ kc_status kc_graph_reserve(kc_graph* g, uint32_t k_max, int pivot, int per_verte
     return count_reserve(g, k_max, pivot, per_vertex, (cudaStream_t)stream);
 }
 
-kc_status kc_count128(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_t subwarp, uint64_t* lo_out,
-                      uint64_t* hi_out, uint32_t* flags_out, void* stream) {
-    clear_error();
-    if (!lo_out) return set_error(KC_E_INVALID_ARG, "lo_out is NULL");
+static kc_status count_sync(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_t subwarp, uint64_t* lo_out,
+                            uint64_t* hi_out, uint64_t* per_vertex_out, uint32_t* flags_out, void* stream) {
+    if (!lo_out) return set_error(KC_E_INVALID_ARG, "total_out is NULL");
     CountArgs a;
     KC_CHECK(resolve(g, k, pivot, scheme, subwarp, a));
-    if (pivot) return set_error(KC_E_UNSUPPORTED, "fixed-k pivoting is not built into this library version");
+    if (per_vertex_out && !pivot)
+        return set_error(KC_E_UNSUPPORTED, "per-vertex counts come from the pivoting traversal (pivot = 1)");
     cudaStream_t s = (cudaStream_t)stream;
-    KC_CHECK(dev_alloc(g->ctl, sizeof(Ctl) + 256));
-    kc_result* rd = (kc_result*)((char*)g->ctl.ptr + 128);
-    KC_CHECK(count_launch(g, a, rd, s));
+    KC_CHECK(dev_alloc(g->result, sizeof(kc_result) + 64));
+    kc_result* rd = (kc_result*)g->result.ptr;
+    uint64_t* pv_dev = nullptr;
+    const bool pv_host = per_vertex_out && !is_device_pointer(per_vertex_out);
+    if (per_vertex_out) {
+        if (pv_host) {
+            KC_CHECK(dev_alloc(g->pv_stage, ((size_t)g->n + 1) * 8));
+            pv_dev = (uint64_t*)g->pv_stage.ptr;
+        } else {
+            pv_dev = per_vertex_out;
+        }
+    }
+    if (pivot) KC_CHECK(count_pivot_async(g, k, rd, pv_dev, s));
+    else KC_CHECK(count_launch(g, a, rd, s));
     kc_result r;
     KC_CUDA(cudaMemcpyAsync(&r, rd, sizeof(r), cudaMemcpyDeviceToHost, s));
+    if (pv_host && g->n) KC_CUDA(cudaMemcpyAsync(per_vertex_out, pv_dev, (size_t)g->n * 8, cudaMemcpyDeviceToHost, s));
     KC_CUDA(cudaStreamSynchronize(s));
     *lo_out = r.total;
     if (hi_out) *hi_out = r.total_hi;
     if (flags_out) *flags_out = r.flags;
     if (r.status != KC_OK) return set_error((kc_status)r.status, "device reported %s", kc_status_name(r.status));
     if (r.flags & (KC_FLAG_TOTAL_OVERFLOW | KC_FLAG_VERTEX_OVERFLOW))
-        return set_error(KC_E_OVERFLOW, "count exceeded 2^64 - 1");
+        return set_error(KC_E_OVERFLOW, "a count exceeded 2^64 - 1");
     return KC_OK;
+}
+
+kc_status kc_count128(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_t subwarp, uint64_t* lo_out,
+                      uint64_t* hi_out, uint32_t* flags_out, void* stream) {
+    clear_error();
+    return count_sync(g, k, pivot, scheme, subwarp, lo_out, hi_out, nullptr, flags_out, stream);
 }
 
 kc_status kc_count(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_t subwarp, uint64_t* total_out,
                    uint64_t* per_vertex_out, uint32_t* flags_out, void* stream) {
     clear_error();
-    if (!total_out) return set_error(KC_E_INVALID_ARG, "total_out is NULL");
-    if (per_vertex_out) return set_error(KC_E_UNSUPPORTED, "per-vertex counts are available from kc_count_all");
     uint64_t hi = 0;
-    return kc_count128(g, k, pivot, scheme, subwarp, total_out, &hi, flags_out, stream);
+    return count_sync(g, k, pivot, scheme, subwarp, total_out, &hi, per_vertex_out, flags_out, stream);
 }
 
 kc_status kc_count_all(kc_graph* g, uint64_t* counts, uint8_t* overflow, uint32_t cap, uint32_t* omega_out,
                        uint32_t per_vertex_k, uint64_t* per_vertex_out, void* stream) {
     clear_error();
-    (void)g; (void)counts; (void)overflow; (void)cap; (void)omega_out; (void)per_vertex_k; (void)per_vertex_out;
-    (void)stream;
-    return set_error(KC_E_UNSUPPORTED, "kc_count_all is not built into this library version");
+    if (!g) return set_error(KC_E_INVALID_ARG, "NULL graph");
+    if (!counts) return set_error(KC_E_INVALID_ARG, "counts is NULL");
+    if (cap == 0) return set_error(KC_E_INVALID_ARG, "cap must be >= 1");
+    if (per_vertex_out && per_vertex_k == 0) return set_error(KC_E_INVALID_ARG, "per_vertex_k must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t* pv_dev = nullptr;
+    const bool pv_host = per_vertex_out && !is_device_pointer(per_vertex_out);
+    if (per_vertex_out) {
+        if (pv_host) {
+            KC_CHECK(dev_alloc(g->pv_stage, ((size_t)g->n + 1) * 8));
+            pv_dev = (uint64_t*)g->pv_stage.ptr;
+        } else {
+            pv_dev = per_vertex_out;
+        }
+    }
+    std::vector<uint8_t> ovf(cap);
+    uint32_t flags = 0, omega = 0;
+    KC_CHECK(count_all_run(g, cap, per_vertex_out ? per_vertex_k : 0, pv_dev, counts, ovf.data(), &omega, &flags, s));
+    if (pv_host && g->n) {
+        KC_CUDA(cudaMemcpyAsync(per_vertex_out, pv_dev, (size_t)g->n * 8, cudaMemcpyDeviceToHost, s));
+        KC_CUDA(cudaStreamSynchronize(s));
+    }
+    if (overflow) memcpy(overflow, ovf.data(), cap);
+    if (omega_out) *omega_out = omega;
+    if (flags & KC_FLAG_TIMEOUT) return set_error(KC_E_TIMEOUT, "time limit reached");
+    if (flags & KC_FLAG_INTERNAL) return set_error(KC_E_INTERNAL, "device-side consistency check failed");
+    bool any = (flags & KC_FLAG_VERTEX_OVERFLOW) != 0;
+    for (uint32_t j = 0; j < cap; ++j) any |= ovf[j] != 0;
+    if (any) return set_error(KC_E_OVERFLOW, "a count exceeded 2^64 - 1");
+    return KC_OK;
 }
 
 }  // extern "C"

@@ -18,6 +18,7 @@
 namespace kc {
 
 kc_status set_error(kc_status s, const char* fmt, ...);
+void note_launch();  // counts every kernel the library launches (kc_launch_count)
 void clear_error();
 kc_status cuda_error(cudaError_t e, const char* what, const char* file, int line);
 
@@ -52,6 +53,8 @@ void dev_free(DevBuf& b);
 struct Ctl {
     unsigned long long total_lo;   // exact 128-bit count, low word
     unsigned long long total_hi;   // carries out of total_lo
+    unsigned long long words;      // bitmap words intersected
+    unsigned long long deadline;   // %globaltimer value after which work stops (0 = none)
     unsigned int flags;            // KC_FLAG_* bits
     unsigned int work_next;        // big-root work counter
     unsigned int work_next_small;  // small-root work counter
@@ -72,6 +75,7 @@ struct kc_graph {
     float orient_ms = 0.f;
     int device = 0;
     int sm_count = 0;
+    double time_limit_s = 0.0;  // 0 = none
     // DAG in the library numbering (vertex r = r-th vertex of the order)
     kc::DevBuf row_ptr;      // u32[n+1]
     kc::DevBuf col;          // u32[m]
@@ -83,7 +87,10 @@ struct kc_graph {
     kc::DevBuf edge_order;   // u32[m] DAG edge ids in work order (EC)
     std::vector<uint64_t> outdeg_hist;  // host: number of vertices per out-degree (d_max + 1 entries)
     // working memory for counting
-    kc::DevBuf ctl;          // kc::Ctl
+    kc::DevBuf ctl;          // kc::Ctl + kernel work counters (sized by kc::ctl_bytes())
+    kc::DevBuf result;       // kc_result written by the synchronous calls
+    kc::DevBuf pivot_out;    // per-size counts of a pivoting run
+    kc::DevBuf pv_stage;     // device staging of per-vertex counts for host outputs
     kc::DevBuf scratch;      // per-block scratch (global-memory bitmaps and stacks)
     kc::DevBuf pv;           // u64 per-vertex accumulators (library numbering) + overflow words
     kc::DevBuf tmp;          // misc temporaries
@@ -121,11 +128,16 @@ struct CountArgs {
 };
 kc_status count_launch(kc_graph* g, const CountArgs& a, kc_result* result_dev, cudaStream_t s);
 kc_status count_reserve(kc_graph* g, uint32_t k_max, int pivot, int per_vertex, cudaStream_t s);
+size_t ctl_bytes();
 
 // kc_pivot.cu
-kc_status count_all_launch(kc_graph* g, uint32_t cap, uint32_t per_vertex_k, uint64_t* per_vertex_dev,
-                           unsigned long long* counts_dev /* 2*cap words: lo,hi per size */, unsigned int* omega_dev,
-                           unsigned int* flags_dev, cudaStream_t s);
+// Fixed-k pivoting count into result_dev (device); per_vertex_dev: n entries
+// (input numbering) or null.
+kc_status count_pivot_async(kc_graph* g, uint32_t k, kc_result* result_dev, uint64_t* per_vertex_dev,
+                            cudaStream_t s);
+// Every size < cap by pivoting; host outputs; synchronises s.
+kc_status count_all_run(kc_graph* g, uint32_t cap, uint32_t pvk, uint64_t* per_vertex_dev, uint64_t* counts_host,
+                        uint8_t* ovf_host, uint32_t* omega_host, uint32_t* flags_host, cudaStream_t s);
 
 int sm_count_of_current_device();
 

@@ -491,6 +491,7 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
 
     if (validate) {
         k_validate_rowptr<<<grid_for(n, 256, sms), 256, 0, s>>>(d_rp, n, nnz, words);
+        note_launch();
         KC_TRY(cudaGetLastError());
         KC_TRY(cudaMemcpyAsync(h_words, words, 4, cudaMemcpyDeviceToHost, s));
         KC_TRY(cudaStreamSynchronize(s));
@@ -498,6 +499,7 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
         if (nnz) {
             uint64_t threads = ((uint64_t)nnz + 7) / 8;
             k_validate_entries<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(d_rp, d_ci, n, nnz, words);
+            note_launch();
             KC_TRY(cudaGetLastError());
         }
         KC_TRY(cudaMemcpyAsync(h_words, words, 4, cudaMemcpyDeviceToHost, s));
@@ -515,6 +517,7 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
     const bool degen = g->orient == KC_ORIENT_DEGENERACY;
     k_degree_key<<<grid_for(n, 256, sms), 256, 0, s>>>(d_rp, n, degen ? nullptr : key, degen ? deg : nullptr,
                                                        degen ? round_of : nullptr, words + 1);
+    note_launch();
     KC_TRY(cudaGetLastError());
     uint32_t max_key = 0;
     if (degen) {
@@ -534,6 +537,7 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
             void* args[] = {(void*)&a_rp, (void*)&a_ci, (void*)&a_n, (void*)&deg, (void*)&round_of,
                             (void*)&a_core, (void*)&F0, (void*)&F1, (void*)&heavy, (void*)&ctl, (void*)&nf_log};
             KC_TRY(cudaLaunchCooperativeKernel((const void*)k_peel, dim3(blocks), dim3(256), args, 0, s));
+            note_launch();
             PeelCtl hc;
             KC_TRY(cudaMemcpyAsync(&hc, ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, s));
             KC_TRY(cudaStreamSynchronize(s));
@@ -567,6 +571,7 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
     KC_TRYS(dev_alloc(g->new_of_old, (size_t)n * 4 + 4));
     KC_TRYS(sort_ids_by_key(key, n, max_key, (uint32_t*)g->old_of_new.ptr, g->tmp, s));
     k_invert<<<grid_for(n, 256, sms), 256, 0, s>>>((uint32_t*)g->old_of_new.ptr, n, (uint32_t*)g->new_of_old.ptr);
+    note_launch();
     KC_TRY(cudaGetLastError());
 
     // out-degrees in the library numbering, then row pointers
@@ -578,6 +583,7 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
     const unsigned fblocks = (unsigned)std::max<uint64_t>(1, (fthreads + 255) / 256);
     if (nnz) {
         k_filter<0><<<fblocks, 256, 0, s>>>(d_rp, d_ci, n, nnz, (uint32_t*)g->new_of_old.ptr, outdeg, nullptr);
+        note_launch();
         KC_TRY(cudaGetLastError());
     }
     uint32_t* drp = (uint32_t*)g->row_ptr.ptr;
@@ -587,14 +593,17 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
     KC_TRY(cudaMemcpyAsync(cursor, drp, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
     if (nnz) {
         k_filter<1><<<fblocks, 256, 0, s>>>(d_rp, d_ci, n, nnz, (uint32_t*)g->new_of_old.ptr, cursor, colbuf);
+        note_launch();
         KC_TRY(cudaGetLastError());
         k_sort_rows<<<grid_for((uint64_t)n * 32, ROWSORT_WARPS * 32, sms), ROWSORT_WARPS * 32, 0, s>>>(
             drp, colbuf, (uint32_t*)g->col.ptr, n);
+        note_launch();
         KC_TRY(cudaGetLastError());
     }
     // d_max, out-degree histogram, root order (out-degree descending)
     KC_TRY(cudaMemsetAsync(words + 2, 0, 4, s));
     k_rowlen_max<<<grid_for(n, 256, sms), 256, 0, s>>>(drp, n, words + 2);
+    note_launch();
     KC_TRY(cudaGetLastError());
     KC_TRY(cudaMemcpyAsync(&h_words[2], words + 2, 4, cudaMemcpyDeviceToHost, s));
     KC_TRY(cudaStreamSynchronize(s));
@@ -602,6 +611,7 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
     unsigned* hist = (unsigned*)heavy;  // n + 1 >= d_max + 1 entries
     KC_TRY(cudaMemsetAsync(hist, 0, ((size_t)g->d_max + 1) * 4, s));
     k_outdeg_from_rowptr<<<grid_for(n, 256, sms), 256, 0, s>>>(drp, n, key, g->d_max, hist);
+    note_launch();
     KC_TRY(cudaGetLastError());
     KC_TRYS(dev_alloc(g->roots, (size_t)n * 4 + 4));
     KC_TRYS(sort_ids_by_key(key, n, g->d_max, (uint32_t*)g->roots.ptr, g->tmp, s));
@@ -633,11 +643,14 @@ kc_status ensure_edge_src(kc_graph* g, cudaStream_t s) {
     uint32_t* off = d + n + 1;
     k_edge_src<<<grid_for((uint64_t)n * 32, 256, sms), 256, 0, s>>>((uint32_t*)g->row_ptr.ptr, n,
                                                                      (uint32_t*)g->edge_src.ptr);
+    note_launch();
     k_root_outdeg<<<grid_for(n, 256, sms), 256, 0, s>>>((uint32_t*)g->row_ptr.ptr, (uint32_t*)g->roots.ptr, n, d);
+    note_launch();
     kc_status st = scan_u32(d, off, n, g->tmp, s);
     if (st == KC_OK) {
         k_edge_order<<<grid_for((uint64_t)n * 32, 256, sms), 256, 0, s>>>(
             (uint32_t*)g->row_ptr.ptr, (uint32_t*)g->roots.ptr, off, n, (uint32_t*)g->edge_order.ptr);
+        note_launch();
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_error(e, "edge order", __FILE__, __LINE__);
     }

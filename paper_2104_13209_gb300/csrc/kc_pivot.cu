@@ -1,0 +1,817 @@
+// Pivoting k-clique counting (Fig. 3; Sections 2.3, 2.4, 3.2, 3.4, 3.5).
+//
+// Level 1 is oriented: root r has candidate set C = N+(r) (ascending library
+// id).  Below it the search runs on the undirected sub-graph induced by C,
+// binary encoded (Section 3.4): adj row i = {j : C[j] adjacent to C[i]}.
+// A tree node holds the candidate set S (a bitmap; every member is adjacent
+// to every vertex on the path), h held vertices (the root included) and q
+// pivots on the path:
+//   S empty            -> leaf (h, q): it stands for the C(q, j - h) cliques of
+//                         size j made of the held vertices plus j - h pivots;
+//   S a clique of size c -> leaf (h, q + c) (every further level would pick a
+//                         pivot adjacent to all the rest);
+//   otherwise          -> pivot p = the member of S with the most neighbours in S
+//                         (ties: lowest index); for each x in S \ N(p), ascending:
+//                         child S' = S ∩ N(x) minus the members of S \ N(p) before x,
+//                         with x held (x != p) or a pivot (x == p).
+// Fixed-k mode (Fig. 3's stopping criterion) skips children with more than k
+// held vertices and subtrees that cannot reach size k.
+//
+// Leaves are counted in an (h, q) histogram in global memory; a final kernel
+// turns it into per-size counts with an exact binomial table (64-bit values,
+// saturation = overflow).  Per-vertex counts for one size k use subtree sums:
+// a held vertex gains C(q, k - h) per leaf below it, a pivot C(q - 1, k - h - 1).
+//
+// Work distribution: big roots (|C| > 32) go to blocks in decreasing
+// out-degree order; the block builds the bitmap, picks the root's pivot, and
+// its warps claim the root's branch subtrees from a per-root counter in
+// global memory (so other blocks can join a large root).  Each warp walks its
+// subtree with warp-parallel pivot selection (lanes over the candidates).
+// Small roots run in warp mode, one warp per root, rows of one 32-bit word.
+#include <algorithm>
+
+#include "kc_bitmap.cuh"
+#include "kc_common.cuh"
+
+namespace kc {
+
+static constexpr int PB = 256;
+static constexpr int PW = PB / 32;
+static constexpr int PSMALL = 32;
+static constexpr uint32_t HDR = 10;  // per-level header words: h, q, p, vtx, held, pad, sumH(2), sumP(2)
+static constexpr unsigned long long SAT = ~0ull;
+
+struct PivotParams {
+    const uint32_t* rp;
+    const uint32_t* col;
+    const uint32_t* roots;       // library ids, decreasing out-degree
+    uint32_t n_big;              // roots[0, n_big): |C| > 32
+    uint32_t n_work;             // roots[n_big, n_work): 32 >= |C| >= dmin
+    uint32_t* task_next;         // per big root: next unclaimed branch (zeroed)
+    uint32_t kfix;               // 0 = every size; else only size kfix is needed
+    uint32_t pvk;                // per-vertex size (0 = none)
+    unsigned long long* pv;      // per-vertex accumulators (library numbering)
+    const unsigned long long* binom;  // C(a, b), a, b < bstride, SAT = >= 2^64 - 1
+    uint32_t bstride;
+    unsigned long long* leaves;  // histogram [h * hq + q]
+    uint32_t hq;
+    uint32_t dcap, wcap;
+    uint32_t lvl_cap;            // stack levels per warp in block mode
+    int adj_in_smem;
+    uint32_t* gstack;            // per-warp stacks for block mode (global)
+    size_t gstack_words;         // words per warp
+    uint32_t* gadj;              // per-block adjacency when it does not fit in shared memory
+    size_t gadj_words;
+    Ctl* ctl;
+};
+
+struct PWorkCtl {
+    unsigned int root_cursor;
+    unsigned int help_lo;
+    unsigned int small_cursor;
+    unsigned int pad;
+};
+
+__device__ __forceinline__ bool p_timed_out(const Ctl* c) {
+    if (c->deadline == 0) return false;
+    if (*(volatile const unsigned*)&c->flags & KC_FLAG_TIMEOUT) return true;
+    if (globaltimer_ns() > c->deadline) {
+        atomicOr((unsigned*)&c->flags, (unsigned)KC_FLAG_TIMEOUT);
+        return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ unsigned long long sat_add(unsigned long long a, unsigned long long b) {
+    unsigned long long s = a + b;
+    return (s < a || a == SAT || b == SAT) ? SAT : s;
+}
+
+__device__ __forceinline__ unsigned long long binom(const PivotParams& P, uint32_t a, int b) {
+    if (b < 0 || (uint32_t)b > a || a >= P.bstride) return 0;
+    return P.binom[(size_t)a * P.bstride + (uint32_t)b];
+}
+
+// per-vertex gain (lane 0 only)
+__device__ __forceinline__ void pv_gain(const PivotParams& P, uint32_t vid, unsigned long long g) {
+    if (g == 0) return;
+    if (g == SAT) {
+        atomicOr(&P.ctl->flags, (unsigned)KC_FLAG_VERTEX_OVERFLOW);
+        return;
+    }
+    unsigned long long old = atomicAdd(&P.pv[vid], g);
+    if (old + g < old) atomicOr(&P.ctl->flags, (unsigned)KC_FLAG_VERTEX_OVERFLOW);
+}
+
+// Run-length cache of leaves in front of the global histogram (lane 0 only).
+struct LeafCache {
+    uint32_t h = 0, q = 0;
+    unsigned long long n = 0;
+    __device__ __forceinline__ void flush(const PivotParams& P) {
+        if (n) {
+            if (h < P.hq && q < P.hq) atomicAdd(&P.leaves[(size_t)h * P.hq + q], n);
+            else atomicOr(&P.ctl->flags, (unsigned)KC_FLAG_INTERNAL);
+        }
+        n = 0;
+    }
+    __device__ __forceinline__ void add(const PivotParams& P, uint32_t hh, uint32_t qq) {
+        if (n && hh == h && qq == q) {
+            ++n;
+            return;
+        }
+        flush(P);
+        h = hh;
+        q = qq;
+        n = 1;
+    }
+};
+
+// Warp-parallel analysis of the node with candidate set S (W words):
+// returns cnt = |S|; kind 0 = empty, 1 = clique, 2 = internal with pivot p.
+__device__ __forceinline__ int analyse(const uint32_t* S, const uint32_t* adj, uint32_t W, uint32_t& cnt,
+                                       uint32_t& p) {
+    const int lane = threadIdx.x & 31;
+    uint32_t c = 0;
+    for (uint32_t w = lane; w < W; w += 32) c += __popc(S[w]);
+    cnt = __reduce_add_sync(0xffffffffu, c);
+    if (cnt == 0) return 0;
+    if (cnt == 1) return 1;
+    uint32_t best = 0, mind = 0xFFFFFFFFu;
+    for (uint32_t w = 0; w < W; ++w) {
+        const uint32_t bits = S[w];
+        if (bits == 0) continue;
+        if (lane < __popc(bits)) {
+            const uint32_t u = (w << 5) + __fns(bits, 0, lane + 1);
+            const uint32_t* au = adj + (size_t)u * W;
+            uint32_t dg = 0;
+            for (uint32_t x = 0; x < W; ++x) dg += __popc(S[x] & au[x]);
+            best = max(best, (dg << 16) | (0xFFFFu - u));
+            mind = min(mind, dg);
+        }
+    }
+    best = __reduce_max_sync(0xffffffffu, best);
+    mind = __reduce_min_sync(0xffffffffu, mind);
+    if (mind == cnt - 1) return 1;
+    p = 0xFFFFu - (best & 0xFFFFu);
+    return 2;
+}
+
+__device__ __forceinline__ uint32_t* lvl_ptr(uint32_t* stk, uint32_t l, uint32_t W) {
+    return stk + (size_t)l * (2 * W + HDR);
+}
+
+// Leaf (h, q) reached by choosing vertex vid (held or pivot); with PV, gains
+// for vid and for the c clique members (pivots of the leaf) in S (if c > 0),
+// and the leaf's contribution to the parent's subtree sums.
+template <bool PV>
+__device__ __forceinline__ void leaf(const PivotParams& P, LeafCache& lc, uint32_t h, uint32_t q, uint32_t vid,
+                                     bool held, const uint32_t* S, uint32_t W, uint32_t c, const uint32_t* cand,
+                                     unsigned long long& sumH, unsigned long long& sumP) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) lc.add(P, h, q);
+    if (PV) {
+        const int k = (int)P.pvk;
+        const unsigned long long gH = binom(P, q, k - (int)h);
+        const unsigned long long gP = q ? binom(P, q - 1, k - (int)h - 1) : 0ull;
+        if (lane == 0) pv_gain(P, vid, held ? gH : gP);
+        if (c && gP) {
+            for (uint32_t w = 0; w < W; ++w) {
+                uint32_t bits = S[w];
+                if (lane < __popc(bits)) pv_gain(P, cand[(w << 5) + __fns(bits, 0, lane + 1)], gP);
+            }
+        }
+        sumH = sat_add(sumH, gH);
+        sumP = sat_add(sumP, gP);
+    }
+}
+
+// Walk the subtree of the start node (candidates S0, h0, q0) reached by
+// choosing vertex vid0 (held0).  stk: this warp's stack (lvl_cap levels).
+// Returns the start node's sumH (per-vertex mode) so the caller can credit
+// the vertices above it.
+template <bool PV>
+__device__ unsigned long long warp_walk(const PivotParams& P, const uint32_t* adj, uint32_t W, const uint32_t* cand,
+                                        uint32_t* stk, uint32_t lvl_cap, const uint32_t* S0, uint32_t h0, uint32_t q0,
+                                        uint32_t vid0, bool held0, LeafCache& lc) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t k = P.kfix;
+    unsigned long long topH = 0, topP = 0;
+    uint32_t* L0 = lvl_ptr(stk, 0, W);
+    for (uint32_t w = lane; w < W; w += 32) L0[w] = S0[w];
+    __syncwarp();
+    uint32_t cnt, p = 0;
+    int kind = analyse(L0, adj, W, cnt, p);
+    if (kind != 2) {
+        const uint32_t c = kind == 1 ? cnt : 0;
+        leaf<PV>(P, lc, h0, q0 + c, vid0, held0, L0, W, c, cand, topH, topP);
+        return topH;
+    }
+    // level 0: S_rem = S0 (already there), P_rem = S0 \ N(p)
+    {
+        const uint32_t* ap = adj + (size_t)p * W;
+        for (uint32_t w = lane; w < W; w += 32) L0[W + w] = L0[w] & ~ap[w];
+        if (lane == 0) {
+            uint32_t* hd = L0 + 2 * W;
+            hd[0] = h0; hd[1] = q0; hd[2] = p; hd[3] = vid0; hd[4] = held0;
+            hd[6] = hd[7] = hd[8] = hd[9] = 0;
+        }
+        __syncwarp();
+    }
+    int l = 0;
+    uint32_t steps = 0;
+    for (;;) {
+        uint32_t* Lc = lvl_ptr(stk, l, W);
+        uint32_t* hd = Lc + 2 * W;
+        const uint32_t x = next_bit(Lc + W, 0, W - 1);
+        if (x == NONE) {
+            // subtree of level l done
+            if (PV) {
+                unsigned long long sH = ((unsigned long long)hd[7] << 32) | hd[6];
+                unsigned long long sP = ((unsigned long long)hd[9] << 32) | hd[8];
+                if (l == 0) {
+                    if (lane == 0) pv_gain(P, hd[3], hd[4] ? sH : sP);
+                    topH = sH;
+                } else {
+                    if (lane == 0) {
+                        pv_gain(P, hd[3], hd[4] ? sH : sP);
+                        uint32_t* ph = lvl_ptr(stk, l - 1, W) + 2 * W;
+                        unsigned long long pH = sat_add(((unsigned long long)ph[7] << 32) | ph[6], sH);
+                        unsigned long long pP = sat_add(((unsigned long long)ph[9] << 32) | ph[8], sP);
+                        ph[6] = (uint32_t)pH; ph[7] = (uint32_t)(pH >> 32);
+                        ph[8] = (uint32_t)pP; ph[9] = (uint32_t)(pP >> 32);
+                    }
+                    __syncwarp();
+                }
+            }
+            if (l == 0) break;
+            --l;
+            continue;
+        }
+        if ((++steps & 4095u) == 0) {
+            int to = lane == 0 ? (int)p_timed_out(P.ctl) : 0;
+            if (__shfl_sync(0xffffffffu, to, 0)) break;
+        }
+        const uint32_t h = hd[0], q = hd[1], piv = hd[2];
+        __syncwarp();
+        if (lane == 0) Lc[W + (x >> 5)] &= ~(1u << (x & 31));  // visited
+        // child candidates: S_rem ∩ N(x); x then leaves S_rem for later siblings
+        uint32_t* Ln = lvl_ptr(stk, l + 1, W);
+        const uint32_t* ax = adj + (size_t)x * W;
+        if ((uint32_t)l + 1 >= lvl_cap) {  // cannot happen: depth <= clique number <= |C| + 1
+            if (lane == 0) atomicOr(&P.ctl->flags, (unsigned)KC_FLAG_INTERNAL);
+            break;
+        }
+        for (uint32_t w = lane; w < W; w += 32) Ln[w] = Lc[w] & ax[w];
+        __syncwarp();
+        if (lane == 0) Lc[x >> 5] &= ~(1u << (x & 31));
+        const bool xheld = x != piv;
+        const uint32_t h2 = h + (xheld ? 1u : 0u), q2 = q + (xheld ? 0u : 1u);
+        if (k && h2 > k) {
+            __syncwarp();
+            continue;
+        }
+        uint32_t cnt2, p2 = 0;
+        int kind2 = analyse(Ln, adj, W, cnt2, p2);
+        if (k && h2 + q2 + cnt2 < k) {
+            __syncwarp();
+            continue;
+        }
+        if (kind2 != 2) {
+            const uint32_t c = kind2 == 1 ? cnt2 : 0;
+            unsigned long long sH = 0, sP = 0;
+            leaf<PV>(P, lc, h2, q2 + c, cand[x], xheld, Ln, W, c, cand, sH, sP);
+            if (PV && lane == 0) {
+                unsigned long long pH = sat_add(((unsigned long long)hd[7] << 32) | hd[6], sH);
+                unsigned long long pP = sat_add(((unsigned long long)hd[9] << 32) | hd[8], sP);
+                hd[6] = (uint32_t)pH; hd[7] = (uint32_t)(pH >> 32);
+                hd[8] = (uint32_t)pP; hd[9] = (uint32_t)(pP >> 32);
+            }
+            __syncwarp();
+            continue;
+        }
+        const uint32_t* ap = adj + (size_t)p2 * W;
+        for (uint32_t w = lane; w < W; w += 32) Ln[W + w] = Ln[w] & ~ap[w];
+        if (lane == 0) {
+            uint32_t* nh = Ln + 2 * W;
+            nh[0] = h2; nh[1] = q2; nh[2] = p2; nh[3] = cand[x]; nh[4] = xheld;
+            nh[6] = nh[7] = nh[8] = nh[9] = 0;
+        }
+        __syncwarp();
+        ++l;
+    }
+    return topH;
+}
+
+// Undirected adjacency of the candidates: OR every row with its transpose.
+template <int NT>
+__device__ void symmetrise(uint32_t* adj, uint32_t d, uint32_t W) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t i = warp; i < d; i += NT / 32) {
+        const uint32_t* ri = adj + (size_t)i * W;
+        for (uint32_t w = lane; w < W; w += 32) {
+            uint32_t bits = ri[w] & ((w << 5) + 31 > i ? 0xFFFFFFFFu : 0u);
+            while (bits) {
+                const uint32_t j = (w << 5) + (__ffs(bits) - 1);
+                bits &= bits - 1;
+                if (j > i) atomicOr(&adj[(size_t)j * W + (i >> 5)], 1u << (i & 31));
+            }
+        }
+    }
+    __syncthreads();
+}
+
+struct PBlockShared {
+    uint32_t slot;
+    uint32_t pivot;
+    uint32_t ntask;
+    uint32_t kind;
+    uint32_t mind;
+    unsigned long long best;
+};
+
+template <bool PV>
+__device__ void pivot_block_phase(const PivotParams& P, uint32_t* smem, PBlockShared& sh, LeafCache& lc) {
+    PWorkCtl* wc = reinterpret_cast<PWorkCtl*>(P.ctl + 1);
+    const uint32_t D0 = (P.dcap + 31) & ~31u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* cand = smem;
+    uint32_t* adj = P.adj_in_smem ? smem + D0 : P.gadj + (size_t)blockIdx.x * P.gadj_words;
+    uint32_t* pre = smem + D0 + (P.adj_in_smem ? (size_t)P.dcap * P.wcap : 0);  // prefix popcounts of P_root
+    uint32_t* Sx = pre + P.wcap + 32 + (size_t)warp * P.wcap;                    // per-warp start set
+    uint32_t* stk = P.gstack + ((size_t)blockIdx.x * PW + warp) * P.gstack_words;
+    int phase = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            uint32_t s = 0xFFFFFFFFu;
+            if (!p_timed_out(P.ctl)) {
+                if (phase == 0) {
+                    s = atomicAdd(&wc->root_cursor, 1u);
+                    if (s >= P.n_big) {
+                        phase = 1;
+                        s = 0xFFFFFFFFu;
+                    }
+                }
+                if (phase == 1) {
+                    uint32_t lo = atomicAdd(&wc->help_lo, 0u);
+                    for (uint32_t probes = 0; lo < P.n_big && probes < 4096; ++lo, ++probes) {
+                        // a root is worth joining while >= 2 branches are unclaimed; the
+                        // branch count is unknown until its pivot is chosen, so use d
+                        const uint32_t u = P.roots[lo];
+                        const uint32_t d = P.rp[u + 1] - P.rp[u];
+                        const uint32_t taken = atomicAdd(&P.task_next[lo], 0u);
+                        if (taken + 2 <= d && taken < 0x7FFFFFFFu) {
+                            s = lo;
+                            break;
+                        }
+                        atomicMax(&wc->help_lo, lo + 1);
+                    }
+                }
+            }
+            sh.slot = s;
+            sh.best = 0;
+            sh.mind = 0xFFFFFFFFu;
+        }
+        __syncthreads();
+        const uint32_t s = sh.slot;
+        if (s == 0xFFFFFFFFu) break;
+        const uint32_t u = P.roots[s];
+        const uint32_t b = P.rp[u], d = P.rp[u + 1] - b;
+        for (uint32_t i = threadIdx.x; i < d; i += PB) cand[i] = P.col[b + i];
+        __syncthreads();
+        const uint32_t W = (d + 31) >> 5;
+        build_bitmap<PB>(P.rp, P.col, cand, d, W, adj);
+        symmetrise<PB>(adj, d, W);
+        // root pivot: the candidate with the most neighbours (all of C is the
+        // root node's candidate set); ties to the lowest index
+        {
+            unsigned long long best = 0;
+            uint32_t mind = 0xFFFFFFFFu;
+            for (uint32_t x = threadIdx.x; x < d; x += PB) {
+                const uint32_t* ax = adj + (size_t)x * W;
+                uint32_t dg = 0;
+                for (uint32_t w = 0; w < W; ++w) dg += __popc(ax[w]);
+                best = max(best, ((unsigned long long)dg << 32) | (0xFFFFFFFFu - x));
+                mind = min(mind, dg);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+                mind = min(mind, __shfl_xor_sync(0xffffffffu, mind, o));
+            }
+            if (lane == 0) {
+                atomicMax(&sh.best, best);
+                atomicMin(&sh.mind, mind);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                sh.pivot = 0xFFFFFFFFu - (uint32_t)(sh.best & 0xFFFFFFFFu);
+                sh.kind = (sh.mind == d - 1) ? 1u : 2u;
+            }
+            __syncthreads();
+        }
+        if (sh.kind == 1) {
+            // the whole candidate set is a clique: one leaf (1, d), taken by one block
+            if (threadIdx.x == 0 && atomicCAS(&P.task_next[s], 0u, 0x80000000u) == 0u) {
+                if (!(P.kfix && 1 + d < P.kfix)) {
+                    lc.add(P, 1, d);
+                    if (PV) {
+                        const int k = (int)P.pvk;
+                        pv_gain(P, u, binom(P, d, k - 1));
+                        const unsigned long long gP = binom(P, d - 1, k - 2);
+                        for (uint32_t i = 0; i < d; ++i) pv_gain(P, cand[i], gP);
+                    }
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+        const uint32_t piv = sh.pivot;
+        const uint32_t* apv = adj + (size_t)piv * W;
+        // branch set of the root: C \ N(p); prefix popcounts of its words
+        if (warp == 0) {
+            uint32_t carry = 0;
+            for (uint32_t w0 = 0; w0 < W; w0 += 32) {
+                const uint32_t w = w0 + lane;
+                uint32_t pr = 0;
+                if (w < W) {
+                    const uint32_t valid = (w == W - 1 && (d & 31)) ? ((1u << (d & 31)) - 1u) : 0xFFFFFFFFu;
+                    pr = ~apv[w] & valid;
+                }
+                const uint32_t c = __popc(pr);
+                uint32_t incl = c;
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (w < W) pre[w] = carry + incl - c;
+                carry += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (lane == 0) {
+                pre[W] = carry;
+                sh.ntask = carry;
+            }
+        }
+        __syncthreads();
+        const uint32_t ntask = sh.ntask;
+        for (;;) {
+            uint32_t t = 0;
+            if (lane == 0) t = atomicAdd(&P.task_next[s], 1u);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= ntask) {
+                // every branch is claimed: keep other blocks from joining this root
+                if (lane == 0) atomicMax(&P.task_next[s], 0x7FFFFFFFu);
+                break;
+            }
+            // the t-th member x of the branch set
+            uint32_t lo = 0, hi = W;  // last word with pre[w] <= t
+            while (hi - lo > 1) {
+                uint32_t mid = (lo + hi) >> 1;
+                if (pre[mid] <= t) lo = mid; else hi = mid;
+            }
+            const uint32_t valid_lo = (lo == W - 1 && (d & 31)) ? ((1u << (d & 31)) - 1u) : 0xFFFFFFFFu;
+            const uint32_t prw = ~apv[lo] & valid_lo;
+            const uint32_t x = (lo << 5) + __fns(prw, 0, t - pre[lo] + 1);
+            const uint32_t* ax = adj + (size_t)x * W;
+            // S_x = C ∩ N(x) minus the branch members before x
+            for (uint32_t w = lane; w < W; w += 32) {
+                const uint32_t valid = (w == W - 1 && (d & 31)) ? ((1u << (d & 31)) - 1u) : 0xFFFFFFFFu;
+                const uint32_t prw2 = ~apv[w] & valid;
+                uint32_t before = 0;
+                if (w < (x >> 5)) before = prw2;
+                else if (w == (x >> 5)) before = prw2 & ((1u << (x & 31)) - 1u);
+                Sx[w] = ax[w] & valid & ~before;
+            }
+            __syncwarp();
+            const bool xheld = x != piv;
+            const uint32_t h0 = 1 + (xheld ? 1u : 0u), q0 = xheld ? 0u : 1u;
+            if (P.kfix && h0 > P.kfix) continue;
+            unsigned long long sH = warp_walk<PV>(P, adj, W, cand, stk, P.lvl_cap, Sx, h0, q0, cand[x], xheld, lc);
+            if (PV && lane == 0) pv_gain(P, u, sH);
+            if (lane == 0 && p_timed_out(P.ctl)) t = 0xFFFFFFFFu;
+            if (__shfl_sync(0xffffffffu, t, 0) == 0xFFFFFFFFu) break;
+        }
+        __syncthreads();
+    }
+}
+
+// Warp mode: one warp per small root, rows of one word.
+struct PWarpShared {
+    uint32_t cand[32];
+    uint32_t adj[32];
+    uint32_t S0[1];
+    uint32_t pad[3];
+    uint32_t stk[(PSMALL + 3) * (2 + HDR)];
+};
+
+template <bool PV>
+__device__ void pivot_warp_phase(const PivotParams& P, PWarpShared& ws, LeafCache& lc) {
+    PWorkCtl* wc = reinterpret_cast<PWorkCtl*>(P.ctl + 1);
+    const int lane = threadIdx.x & 31;
+    uint32_t iter = 0;
+    for (;;) {
+        uint32_t i = 0;
+        if (lane == 0) {
+            i = P.n_big + atomicAdd(&wc->small_cursor, 1u);
+            if ((++iter & 63u) == 0 && p_timed_out(P.ctl)) i = 0xFFFFFFFFu;
+        }
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= P.n_work) break;
+        const uint32_t u = P.roots[i];
+        const uint32_t b = P.rp[u];
+        const uint32_t d = P.rp[u + 1] - b;
+        if (lane < (int)d) ws.cand[lane] = P.col[b + lane];
+        __syncwarp();
+        const uint32_t last = ws.cand[d - 1];
+        uint32_t myrow = 0;
+        for (uint32_t r = 0; r < d; ++r) {
+            const uint32_t x = ws.cand[r];
+            const uint32_t xb = P.rp[x], xe = P.rp[x + 1];
+            uint32_t bits = 0;
+            for (uint32_t j0 = xb; j0 < xe; j0 += 32) {
+                uint32_t j = j0 + lane;
+                uint32_t y = j < xe ? P.col[j] : NONE;
+                if (y != NONE && y <= last) {
+                    uint32_t pos = find_sorted(ws.cand, r + 1, d, y);
+                    if (pos != NONE) bits |= 1u << pos;
+                }
+                if (__shfl_sync(0xffffffffu, y, 31) >= last) break;
+            }
+            bits = __reduce_or_sync(0xffffffffu, bits);
+            if (lane == (int)r) myrow = bits;
+        }
+        // undirected row of candidate `lane`: its out-row plus the rows that name it
+        uint32_t colbits = 0;
+        for (uint32_t r = 0; r < d; ++r) {
+            uint32_t rr = __shfl_sync(0xffffffffu, myrow, r);
+            if ((rr >> lane) & 1u) colbits |= 1u << r;
+        }
+        if (lane < (int)d) ws.adj[lane] = myrow | colbits;
+        if (lane == 0) ws.S0[0] = d == 32 ? 0xFFFFFFFFu : ((1u << d) - 1u);
+        __syncwarp();
+        warp_walk<PV>(P, ws.adj, 1, ws.cand, ws.stk, PSMALL + 3, ws.S0, 1, 0, u, true, lc);
+        __syncwarp();
+    }
+}
+
+template <bool PV>
+__global__ void __launch_bounds__(PB) k_count_pivot(const PivotParams P) {
+    extern __shared__ __align__(16) uint32_t psmem[];
+    __shared__ PBlockShared sh;
+    LeafCache lc;
+    if (P.n_big > 0) pivot_block_phase<PV>(P, psmem, sh, lc);
+    __syncthreads();
+    if (P.n_work > P.n_big) {
+        PWarpShared* ws = reinterpret_cast<PWarpShared*>(psmem) + (threadIdx.x >> 5);
+        pivot_warp_phase<PV>(P, *ws, lc);
+    }
+    if ((threadIdx.x & 31) == 0) lc.flush(P);
+}
+
+// C(a, b) for a, b < B, saturating at SAT (one block, row by row).
+__global__ void k_binom(unsigned long long* t, uint32_t B) {
+    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) t[b] = b == 0 ? 1ull : 0ull;
+    __syncthreads();
+    for (uint32_t a = 1; a < B; ++a) {
+        for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) {
+            unsigned long long x = b ? t[(size_t)(a - 1) * B + b - 1] : 0ull;
+            unsigned long long y = t[(size_t)(a - 1) * B + b];
+            t[(size_t)a * B + b] = b == 0 ? 1ull : sat_add(x, y);
+        }
+        __syncthreads();
+    }
+}
+
+// counts[j] = sum over (h, q) of leaves[h][q] * C(q, j - h); omega = max h + q.
+__global__ void k_pivot_reduce(const unsigned long long* leaves, uint32_t hq, const unsigned long long* binom_t,
+                               uint32_t B, uint32_t cap, uint32_t kfix, unsigned long long n, unsigned long long m,
+                               unsigned long long* counts, unsigned char* ovf, unsigned int* omega) {
+    for (uint32_t j = threadIdx.x + blockIdx.x * blockDim.x; j < cap; j += gridDim.x * blockDim.x) {
+        unsigned long long s = 0;
+        bool o = false;
+        if (j == 0) s = 1;
+        else if (j == 1) s = n;
+        else if (j == 2) s = m;
+        else if (kfix == 0 || j == kfix) {
+            for (uint32_t h = 1; h <= j && h < hq; ++h) {
+                for (uint32_t q = j - h; q < hq; ++q) {
+                    const unsigned long long L = leaves[(size_t)h * hq + q];
+                    if (!L) continue;
+                    const unsigned long long c = (q < B && j - h < B) ? binom_t[(size_t)q * B + (j - h)] : SAT;
+                    if (c == SAT) { o = true; continue; }
+                    const unsigned long long lo = L * c;
+                    if (__umul64hi(L, c) != 0) o = true;
+                    const unsigned long long t = s + lo;
+                    if (t < s) o = true;
+                    s = t;
+                }
+            }
+        }
+        counts[j] = s;
+        ovf[j] = o ? 1 : 0;
+    }
+    if (blockIdx.x == 0) {
+        unsigned int w = 0;
+        for (size_t x = threadIdx.x; x < (size_t)hq * hq; x += blockDim.x)
+            if (leaves[x]) w = max(w, (unsigned)(x / hq + x % hq));
+        for (int o = 16; o > 0; o >>= 1) w = max(w, __shfl_xor_sync(0xffffffffu, w, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(omega, w);
+    }
+}
+
+__global__ void k_pivot_pv_small(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t k,
+                                 unsigned long long* pv) {
+    // k = 1: every vertex is in one 1-clique; k = 2: its degree (out + in)
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (k == 1) pv[v] = 1;
+        else atomicAdd(&pv[v], (unsigned long long)(rp[v + 1] - rp[v]));
+    }
+    if (k == 2)
+        for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+            for (uint32_t e = rp[v]; e < rp[v + 1]; ++e) atomicAdd(&pv[col[e]], 1ull);
+}
+
+__global__ void k_map_pv(const unsigned long long* pv, const uint32_t* new_of_old, uint32_t n,
+                         unsigned long long* out) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        out[v] = pv[new_of_old[v]];
+}
+
+__global__ void k_pivot_set_deadline(Ctl* ctl, unsigned long long budget_ns) {
+    ctl->deadline = budget_ns ? globaltimer_ns() + budget_ns : 0ull;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static uint64_t roots_at_least(const kc_graph* g, uint64_t dmin) {
+    uint64_t c = 0;
+    for (uint64_t d = dmin; d < g->outdeg_hist.size(); ++d) c += g->outdeg_hist[d];
+    return c;
+}
+
+static constexpr size_t PSMEM_LIMIT = 220 * 1024;
+
+static kc_status pivot_run(kc_graph* g, uint32_t kfix, uint32_t cap, uint32_t pvk, uint64_t* per_vertex_dev,
+                           unsigned long long* counts_dev, unsigned char* ovf_dev, unsigned int* omega_dev,
+                           unsigned int* flags_dev, cudaStream_t s) {
+    const int sms = g->sm_count;
+    const uint32_t n = g->n;
+    const uint32_t dcap = std::max<uint32_t>(g->d_max, 1);
+    const uint32_t wcap = (dcap + 31) / 32;
+    if (dcap >= 0xFFFFu) return set_error(KC_E_UNSUPPORTED, "pivoting supports out-degrees below 65535");
+    const uint32_t hq = dcap + 3;        // h, q <= clique number <= d_max + 1
+    const uint32_t B = std::max<uint32_t>(dcap + 3, cap + 2);
+    const uint32_t dmin = kfix ? std::max<uint32_t>(2, kfix - 1) : 2;
+    const uint64_t n_work = roots_at_least(g, dmin);
+    const uint64_t n_big = roots_at_least(g, std::max<uint32_t>(PSMALL + 1, dmin));
+    // memory: ctl, leaves, binomials, per-root task counters, per-vertex accumulators
+    KC_CHECK(dev_alloc(g->ctl, ctl_bytes()));
+    Ctl* ctl = (Ctl*)g->ctl.ptr;
+    const size_t leaves_b = (size_t)hq * hq * 8, binom_b = (size_t)B * B * 8;
+    const size_t tasks_b = ((size_t)n_big + 16) * 4, pv_b = pvk ? ((size_t)n + 16) * 8 : 0;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    KC_CHECK(dev_alloc(g->pv, al(leaves_b) + al(binom_b) + al(tasks_b) + al(pv_b)));
+    char* p = (char*)g->pv.ptr;
+    unsigned long long* leaves = (unsigned long long*)p; p += al(leaves_b);
+    unsigned long long* binom_t = (unsigned long long*)p; p += al(binom_b);
+    uint32_t* tasks = (uint32_t*)p; p += al(tasks_b);
+    unsigned long long* pv = pvk ? (unsigned long long*)p : nullptr;
+    KC_CUDA(cudaMemsetAsync(ctl, 0, ctl_bytes(), s));
+    KC_CUDA(cudaMemsetAsync(leaves, 0, leaves_b, s));
+    KC_CUDA(cudaMemsetAsync(tasks, 0, tasks_b, s));
+    if (pv) KC_CUDA(cudaMemsetAsync(pv, 0, pv_b, s));
+    k_binom<<<1, 1024, 0, s>>>(binom_t, B);
+    note_launch();
+    KC_CUDA(cudaGetLastError());
+    unsigned long long budget = g->time_limit_s > 0 ? (unsigned long long)(g->time_limit_s * 1e9) : 0ull;
+    k_pivot_set_deadline<<<1, 1, 0, s>>>(ctl, budget);
+    note_launch();
+    KC_CUDA(cudaGetLastError());
+    // geometry
+    const size_t D0 = (dcap + 31) & ~31u;
+    const size_t adj_w = (size_t)dcap * wcap;
+    const size_t tail_w = wcap + 32 + (size_t)PW * wcap;
+    size_t smem_w = D0 + adj_w + tail_w;
+    int adj_in_smem = 1;
+    if (smem_w * 4 > PSMEM_LIMIT) {
+        adj_in_smem = 0;
+        smem_w = D0 + tail_w;
+    }
+    size_t smem = std::max(smem_w * 4, sizeof(PWarpShared) * PW);
+    const bool pvon = pv != nullptr && pvk >= 3;
+    void (*kern)(const PivotParams) = pvon ? k_count_pivot<true> : k_count_pivot<false>;
+    KC_CUDA(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int bps = 0;
+    KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, PB, smem));
+    if (bps < 1) return set_error(KC_E_UNSUPPORTED, "pivot kernel cannot be resident (smem %zu)", smem);
+    const int blocks = bps * sms;
+    const uint32_t lvl_cap = dcap + 3;
+    const size_t gstack_words = ((size_t)lvl_cap * (2 * wcap + HDR) + 63) & ~(size_t)63;
+    const size_t gadj_words = adj_in_smem ? 0 : ((adj_w + 63) & ~(size_t)63);
+    KC_CHECK(dev_alloc(g->scratch, ((size_t)blocks * PW * gstack_words + (size_t)blocks * gadj_words + 64) * 4));
+    PivotParams P;
+    memset(&P, 0, sizeof(P));
+    P.rp = (const uint32_t*)g->row_ptr.ptr;
+    P.col = (const uint32_t*)g->col.ptr;
+    P.roots = (const uint32_t*)g->roots.ptr;
+    P.n_big = (uint32_t)n_big;
+    P.n_work = (uint32_t)n_work;
+    P.task_next = tasks;
+    P.kfix = kfix;
+    P.pvk = pvon ? pvk : 0;
+    P.pv = pv;
+    P.binom = binom_t;
+    P.bstride = B;
+    P.leaves = leaves;
+    P.hq = hq;
+    P.dcap = dcap;
+    P.wcap = wcap;
+    P.lvl_cap = lvl_cap;
+    P.adj_in_smem = adj_in_smem;
+    P.gstack = (uint32_t*)g->scratch.ptr;
+    P.gstack_words = gstack_words;
+    P.gadj = (uint32_t*)g->scratch.ptr + (size_t)blocks * PW * gstack_words;
+    P.gadj_words = gadj_words;
+    P.ctl = ctl;
+    if (n_work > 0) {
+        kern<<<blocks, PB, smem, s>>>(P);
+        note_launch();
+        KC_CUDA(cudaGetLastError());
+    }
+    if (pv && pvk < 3) {
+        k_pivot_pv_small<<<std::max(1, sms * 4), 256, 0, s>>>(P.rp, P.col, n, pvk, pv);
+        note_launch();
+        KC_CUDA(cudaGetLastError());
+    }
+    KC_CUDA(cudaMemsetAsync(omega_dev, 0, 4, s));
+    k_pivot_reduce<<<std::max<uint32_t>(1, (cap + 255) / 256), 256, 0, s>>>(leaves, hq, binom_t, B, cap, kfix, n, g->m,
+                                                                            counts_dev, ovf_dev, omega_dev);
+    note_launch();
+    KC_CUDA(cudaGetLastError());
+    if (per_vertex_dev && pv) {
+        k_map_pv<<<std::max(1, sms * 4), 256, 0, s>>>(pv, (const uint32_t*)g->new_of_old.ptr, n,
+                                                       (unsigned long long*)per_vertex_dev);
+        note_launch();
+        KC_CUDA(cudaGetLastError());
+    }
+    KC_CUDA(cudaMemcpyAsync(flags_dev, &ctl->flags, 4, cudaMemcpyDeviceToDevice, s));
+    return KC_OK;
+}
+
+__global__ void k_pack_pivot_result(const unsigned long long* counts, const unsigned char* ovf, const unsigned* flags,
+                                    uint32_t k, kc_result* out) {
+    kc_result r;
+    r.total = counts[k];
+    r.total_hi = 0;
+    r.flags = *flags | (ovf[k] ? KC_FLAG_TOTAL_OVERFLOW : 0u);
+    r.status = (*flags & KC_FLAG_TIMEOUT) ? KC_E_TIMEOUT : ((*flags & KC_FLAG_INTERNAL) ? KC_E_INTERNAL : KC_OK);
+    r.words = 0;
+    *out = r;
+}
+
+// Output area of a pivoting run: counts[cap] u64, ovf[cap] u8, omega, flags.
+static kc_status pivot_out(kc_graph* g, uint32_t cap, unsigned long long*& counts, unsigned char*& ovf,
+                           unsigned int*& omega, unsigned int*& flags) {
+    const size_t cb = ((size_t)cap * 8 + 255) & ~(size_t)255, ob = ((size_t)cap + 255) & ~(size_t)255;
+    KC_CHECK(dev_alloc(g->pivot_out, cb + ob + 256));
+    char* p = (char*)g->pivot_out.ptr;
+    counts = (unsigned long long*)p;
+    ovf = (unsigned char*)(p + cb);
+    omega = (unsigned int*)(p + cb + ob);
+    flags = omega + 1;
+    return KC_OK;
+}
+
+kc_status count_pivot_async(kc_graph* g, uint32_t k, kc_result* result_dev, uint64_t* per_vertex_dev,
+                            cudaStream_t s) {
+    unsigned long long* counts;
+    unsigned char* ovf;
+    unsigned int *omega, *flags;
+    KC_CHECK(pivot_out(g, k + 1, counts, ovf, omega, flags));
+    KC_CHECK(pivot_run(g, k, k + 1, per_vertex_dev ? k : 0, per_vertex_dev, counts, ovf, omega, flags, s));
+    k_pack_pivot_result<<<1, 1, 0, s>>>(counts, ovf, flags, k, result_dev);
+    note_launch();
+    KC_CUDA(cudaGetLastError());
+    return KC_OK;
+}
+
+kc_status count_all_run(kc_graph* g, uint32_t cap, uint32_t pvk, uint64_t* per_vertex_dev, uint64_t* counts_host,
+                        uint8_t* ovf_host, uint32_t* omega_host, uint32_t* flags_host, cudaStream_t s) {
+    unsigned long long* counts;
+    unsigned char* ovf;
+    unsigned int *omega, *flags;
+    KC_CHECK(pivot_out(g, cap, counts, ovf, omega, flags));
+    KC_CHECK(pivot_run(g, 0, cap, pvk, per_vertex_dev, counts, ovf, omega, flags, s));
+    KC_CUDA(cudaMemcpyAsync(counts_host, counts, (size_t)cap * 8, cudaMemcpyDeviceToHost, s));
+    if (ovf_host) KC_CUDA(cudaMemcpyAsync(ovf_host, ovf, cap, cudaMemcpyDeviceToHost, s));
+    unsigned int of[2];
+    KC_CUDA(cudaMemcpyAsync(of, omega, 8, cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    uint32_t om = of[0];
+    if (g->m > 0 && om < 2) om = 2;
+    if (g->n > 0 && om < 1) om = 1;
+    if (omega_host) *omega_host = om;
+    if (flags_host) *flags_host = of[1];
+    return KC_OK;
+}
+
+}  // namespace kc

@@ -94,12 +94,14 @@ size_t scan_tmp_bytes(size_t n) {
 static kc_status scan_rec(const uint32_t* in, uint32_t* out, size_t n, char* tmp, cudaStream_t s) {
     if (n == 0) {
         k_write_zero_total<<<1, 1, 0, s>>>(out);
+        note_launch();
         KC_CUDA(cudaGetLastError());
         return KC_OK;
     }
     size_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (nt == 1) {
         k_tile_scan<<<1, SCAN_THREADS, 0, s>>>(in, n, nullptr, out);
+        note_launch();
         KC_CUDA(cudaGetLastError());
         return KC_OK;
     }
@@ -107,9 +109,11 @@ static kc_status scan_rec(const uint32_t* in, uint32_t* out, size_t n, char* tmp
     uint32_t* offs = sums + nt;
     char* next = (char*)(offs + nt + 1 + 64);
     k_tile_reduce<<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, sums);
+    note_launch();
     KC_CUDA(cudaGetLastError());
     KC_CHECK(scan_rec(sums, offs, nt, next, s));
     k_tile_scan<<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, offs, out);
+    note_launch();
     KC_CUDA(cudaGetLastError());
     return KC_OK;
 }

@@ -93,9 +93,11 @@ kc_status sort_ids_by_key(const uint32_t* key, uint32_t n, uint32_t max_key, uin
         uint32_t* kout = (ps & 1) ? kb : ka;
         uint32_t* vout = (ps == passes - 1) ? out_ids : ((ps & 1) ? vb : va);
         k_radix_hist<<<blocks, SORT_WARPS * 32, 0, s>>>(kin, key, n, shift, ntiles, hist);
+        note_launch();
         KC_CUDA(cudaGetLastError());
         KC_CHECK(scan_u32_raw(hist, offs, hist_n, stmp, s));
         k_radix_scatter<<<blocks, SORT_WARPS * 32, 0, s>>>(kin, key, vin, n, shift, ntiles, offs, kout, vout);
+        note_launch();
         KC_CUDA(cudaGetLastError());
         kin = kout;
         vin = vout;

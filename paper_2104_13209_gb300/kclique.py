@@ -45,6 +45,7 @@ _SCHEME = {"auto": KC_SCHEME_AUTO, "vc": KC_SCHEME_VC, "ec": KC_SCHEME_EC}
 EXPORTED = [
     "kc_last_error", "kc_status_name", "kc_version", "kc_graph_create", "kc_graph_destroy", "kc_graph_info_get",
     "kc_graph_export", "kc_count", "kc_count128", "kc_count_async", "kc_graph_reserve", "kc_count_all",
+    "kc_graph_set_time_limit", "kc_launch_count",
 ]
 
 
@@ -56,7 +57,7 @@ class kc_graph_info(ctypes.Structure):
 
 class kc_result(ctypes.Structure):
     _fields_ = [("total", ctypes.c_uint64), ("total_hi", ctypes.c_uint64), ("flags", ctypes.c_uint32),
-                ("status", ctypes.c_uint32)]
+                ("status", ctypes.c_uint32), ("words", ctypes.c_uint64)]
 
 
 RESULT_BYTES = ctypes.sizeof(kc_result)
@@ -93,6 +94,8 @@ def load(build_if_missing: bool = False):
     lib.kc_status_name.restype = ctypes.c_char_p
     lib.kc_status_name.argtypes = [i32]
     lib.kc_version.restype = i32
+    lib.kc_launch_count.restype = u64
+    lib.kc_launch_count.argtypes = []
     lib.kc_graph_create.argtypes = [vp, vp, u32, u64, i32, i32, i32, vp, ctypes.POINTER(vp)]
     lib.kc_graph_destroy.argtypes = [vp]
     lib.kc_graph_info_get.argtypes = [vp, ctypes.POINTER(kc_graph_info)]
@@ -103,8 +106,9 @@ def load(build_if_missing: bool = False):
     lib.kc_count_async.argtypes = [vp, u32, i32, i32, u32, vp, vp, vp]
     lib.kc_graph_reserve.argtypes = [vp, u32, i32, i32, vp]
     lib.kc_count_all.argtypes = [vp, vp, vp, u32, ctypes.POINTER(u32), u32, vp, vp]
+    lib.kc_graph_set_time_limit.argtypes = [vp, ctypes.c_double]
     for f in ("kc_graph_create", "kc_graph_destroy", "kc_graph_info_get", "kc_graph_export", "kc_count",
-              "kc_count128", "kc_count_async", "kc_graph_reserve", "kc_count_all"):
+              "kc_count128", "kc_count_async", "kc_graph_reserve", "kc_count_all", "kc_graph_set_time_limit"):
         getattr(lib, f).restype = i32
     _lib = lib
     return lib
@@ -115,6 +119,11 @@ def status_name(s: int) -> str:
         return load().kc_status_name(s).decode()
     except Exception:  # library not loadable: plain number
         return f"status {s}"
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().kc_launch_count())
 
 
 def last_error() -> str:
@@ -156,6 +165,7 @@ class CountResult:
     total: int            # exact count (both words)
     flags: int
     overflow: bool        # exceeded 2^64 - 1
+    words: int = 0        # bitmap words intersected by the traversal
 
     @property
     def total_u64(self) -> int:
@@ -202,6 +212,9 @@ class Graph:
         _check(load().kc_graph_info_get(self._h, ctypes.byref(i)))
         return {f: getattr(i, f) for f, _ in kc_graph_info._fields_}
 
+    def set_time_limit(self, seconds: float):
+        _check(load().kc_graph_set_time_limit(self._h, float(seconds)))
+
     def export(self, core: bool = False):
         """(dag_row_ptr, dag_col, new_of_old, core or None) as numpy arrays."""
         inf = self.info()
@@ -219,7 +232,28 @@ class Graph:
         _check(load().kc_count128(self._h, k, int(pivot), _SCHEME[scheme], subwarp, ctypes.byref(lo), ctypes.byref(hi),
                                   ctypes.byref(fl), _stream_ptr(stream)), allow=(KC_OK, KC_E_OVERFLOW))
         total = (hi.value << 64) | lo.value
-        return CountResult(total, fl.value, total >= (1 << 64))
+        return CountResult(total, fl.value, total >= (1 << 64) or bool(fl.value & KC_FLAG_TOTAL_OVERFLOW))
+
+    def count_per_vertex(self, k: int, pivot: bool = True, scheme: str = "auto", stream=None):
+        """(total mod 2^64, per-vertex counts mod 2^64 as uint64[n], flags) via kc_count."""
+        tot, fl = ctypes.c_uint64(), ctypes.c_uint32()
+        pv = np.zeros(max(self.n, 1), dtype=np.uint64)
+        _check(load().kc_count(self._h, k, int(pivot), _SCHEME[scheme], 0, ctypes.byref(tot), pv.ctypes.data,
+                               ctypes.byref(fl), _stream_ptr(stream)), allow=(KC_OK, KC_E_OVERFLOW))
+        return tot.value, pv[: self.n], fl.value
+
+    def count_all(self, cap: int | None = None, per_vertex_k: int = 0, stream=None):
+        """Every clique size by pivoting: (counts uint64[cap], overflow uint8[cap], omega, per-vertex or None)."""
+        if cap is None:
+            cap = self.info()["d_max"] + 3
+        counts = np.zeros(cap, dtype=np.uint64)
+        ovf = np.zeros(cap, dtype=np.uint8)
+        om = ctypes.c_uint32()
+        pv = np.zeros(max(self.n, 1), dtype=np.uint64) if per_vertex_k else None
+        _check(load().kc_count_all(self._h, counts.ctypes.data, ovf.ctypes.data, cap, ctypes.byref(om), per_vertex_k,
+                                   pv.ctypes.data if pv is not None else None, _stream_ptr(stream)),
+               allow=(KC_OK, KC_E_OVERFLOW))
+        return counts, ovf, om.value, (pv[: self.n] if pv is not None else None)
 
     def count_async(self, k: int, result_dev, pivot: bool = False, scheme: str = "auto", subwarp: int = 0,
                     stream=None):
@@ -238,4 +272,4 @@ def parse_result(raw: bytes) -> CountResult:
     if r.status != KC_OK:
         raise KCError(r.status, "device-side failure")
     total = (r.total_hi << 64) | r.total
-    return CountResult(total, r.flags, total >= (1 << 64))
+    return CountResult(total, r.flags, total >= (1 << 64), r.words)

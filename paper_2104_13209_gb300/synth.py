@@ -286,3 +286,53 @@ def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c:
         src = (src << 1) | bit_s
         dst = (dst << 1) | bit_d
     return edges_to_csr(n, src, dst, f"RMAT{scale}-ef{edge_factor}s{seed}")
+
+
+# ----------------------------------------------------------------------------
+# Chung-Lu power-law graph with planted dense communities
+# ----------------------------------------------------------------------------
+
+def chung_lu_planted(n: int, beta: float = 2.1, mean_deg: float = 30.0, ncomm: int = 0, size_min: int = 40,
+                     size_max: int = 200, p_in: float = 0.9, seed: int = 0) -> CSRGraph:
+    """Power-law background plus vertex-disjoint dense communities.
+
+    Background (the fast Chung-Lu sampler of Pinar, Seshadhri and Kolda, 2012):
+    weights w_i proportional to (i + 1)^(-1/(beta - 1)), scaled to mean
+    ``mean_deg`` and capped at sqrt(sum w); round(sum(w) / 2) edges whose two
+    endpoints are drawn independently with probability proportional to w
+    (streams (seed, 0xC1) and (seed, 0xC2)).  Communities: ``ncomm`` groups with
+    sizes uniform in [size_min, size_max] (stream (seed, 0xC3)) taken as
+    consecutive blocks of a seeded permutation (so they are vertex-disjoint),
+    each pair inside a group an edge with probability p_in (stream
+    (seed, 0xC4), one counter per pair).  Loops and duplicates are removed.
+    """
+    i = np.arange(n, dtype=np.float64)
+    w = (i + 1.0) ** (-1.0 / (beta - 1.0))
+    w *= mean_deg * n / w.sum()
+    w = np.minimum(w, math.sqrt(w.sum()))
+    m = int(round(w.sum() / 2))
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    cnt = np.arange(m, dtype=np.uint64)
+    u = np.searchsorted(cdf, uniform(stream_key(seed, 0xC1), cnt), side="right")
+    v = np.searchsorted(cdf, uniform(stream_key(seed, 0xC2), cnt), side="right")
+    u = np.minimum(u, n - 1)
+    v = np.minimum(v, n - 1)
+    us, vs = [u], [v]
+    if ncomm:
+        sizes = size_min + np.floor(uniform(stream_key(seed, 0xC3), np.arange(ncomm, dtype=np.uint64)) *
+                                    (size_max - size_min + 1)).astype(np.int64)
+        if sizes.sum() > n:
+            raise ValueError("communities do not fit in the graph")
+        perm = random_permutation(n, seed, 0xC5)
+        key = stream_key(seed, 0xC4)
+        start, pair_base = 0, 0
+        for s in sizes.tolist():
+            members = perm[start:start + s]
+            a, b = np.triu_indices(s, 1)
+            keep = uniform(key, np.arange(pair_base, pair_base + a.size, dtype=np.uint64)) < p_in
+            us.append(members[a[keep]])
+            vs.append(members[b[keep]])
+            start += s
+            pair_base += a.size
+    return edges_to_csr(n, np.concatenate(us), np.concatenate(vs), f"CL{n}-b{beta}-d{mean_deg}-c{ncomm}s{seed}")

@@ -85,7 +85,7 @@ typedef struct kc_result {
     uint64_t total_hi;     /* high 64 bits (non-zero iff the count overflowed uint64) */
     uint32_t flags;        /* KC_FLAG_* */
     uint32_t status;       /* KC_OK or the kc_status of a device-side failure */
-    uint64_t words;        /* 32-bit bitmap words intersected (AND + popcount) by the traversal */
+    uint64_t words;        /* work units: bitmap words intersected (orientation) or tree nodes (pivoting) */
 } kc_result;
 
 /* ---- errors -------------------------------------------------------------- */
@@ -125,6 +125,12 @@ kc_status kc_graph_info_get(const kc_graph* g, kc_graph_info* out);
  * The device checks the budget between work items and every few thousand
  * tree nodes, so it may be overrun by a fraction of a millisecond. */
 kc_status kc_graph_set_time_limit(kc_graph* g, double seconds);
+
+/* Work units of the last synchronous count on this graph (kc_count,
+ * kc_count128, kc_count_all): for the graph-orientation traversal the 32-bit
+ * bitmap words intersected (one AND plus one popcount each); for pivoting the
+ * search-tree nodes analysed (a pivot search each). */
+kc_status kc_graph_last_work(const kc_graph* g, uint64_t* units);
 
 /* Copy the oriented graph to host memory (for inspection and tests).
  *   dag_row_ptr[n+1], dag_col[num_edges]: the DAG in the library's vertex

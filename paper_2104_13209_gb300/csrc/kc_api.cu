@@ -31,10 +31,9 @@ kc_status set_error(kc_status s, const char* fmt, ...) {
 void clear_error() { t_err.clear(); }
 
 kc_status cuda_error(cudaError_t e, const char* what, const char* file, int line) {
-    if (e == cudaErrorMemoryAllocation) {
-        cudaGetLastError();
+    cudaGetLastError();  // a non-sticky error must not leak into the next call
+    if (e == cudaErrorMemoryAllocation)
         return set_error(KC_E_NO_MEMORY, "out of device memory in %s (%s:%d)", what, file, line);
-    }
     return set_error(KC_E_CUDA, "CUDA error %d (%s) in %s (%s:%d)", (int)e, cudaGetErrorString(e), what, file, line);
 }
 
@@ -194,6 +193,13 @@ kc_status kc_graph_set_time_limit(kc_graph* g, double seconds) {
     return KC_OK;
 }
 
+kc_status kc_graph_last_work(const kc_graph* g, uint64_t* units) {
+    clear_error();
+    if (!g || !units) return set_error(KC_E_INVALID_ARG, "NULL argument");
+    *units = g->last_work;
+    return KC_OK;
+}
+
 kc_status kc_graph_export(const kc_graph* g, uint32_t* dag_row_ptr, uint32_t* dag_col, uint32_t* new_of_old,
                           uint32_t* core) {
     clear_error();
@@ -277,6 +283,7 @@ static kc_status count_sync(kc_graph* g, uint32_t k, int pivot, int scheme, uint
     KC_CUDA(cudaMemcpyAsync(&r, rd, sizeof(r), cudaMemcpyDeviceToHost, s));
     if (pv_host && g->n) KC_CUDA(cudaMemcpyAsync(per_vertex_out, pv_dev, (size_t)g->n * 8, cudaMemcpyDeviceToHost, s));
     KC_CUDA(cudaStreamSynchronize(s));
+    g->last_work = r.words;
     *lo_out = r.total;
     if (hi_out) *hi_out = r.total_hi;
     if (flags_out) *flags_out = r.flags;

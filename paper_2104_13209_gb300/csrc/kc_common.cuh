@@ -76,6 +76,7 @@ struct kc_graph {
     int device = 0;
     int sm_count = 0;
     double time_limit_s = 0.0;  // 0 = none
+    uint64_t last_work = 0;     // work units of the last synchronous count
     // DAG in the library numbering (vertex r = r-th vertex of the order)
     kc::DevBuf row_ptr;      // u32[n+1]
     kc::DevBuf col;          // u32[m]
@@ -109,10 +110,11 @@ size_t scan_tmp_bytes(size_t n);
 // Same, with caller-provided scratch of scan_tmp_bytes(n) bytes.
 kc_status scan_u32_raw(const uint32_t* in, uint32_t* out, size_t n, void* tmp, cudaStream_t s);
 
-// kc_sort.cu: stable sort of the ids 0..n-1 by key[id] (ascending; equal keys
-// keep id order).  out_ids receives the sorted ids.  max_key bounds the keys.
+// kc_sort.cu: stable sort of the ids 0..n-1 (or of in_ids[0..n) when given)
+// by key[id], ascending; equal keys keep their input order.  out_ids receives
+// the sorted ids (it must not alias in_ids).  max_key bounds the keys.
 kc_status sort_ids_by_key(const uint32_t* key, uint32_t n, uint32_t max_key, uint32_t* out_ids, DevBuf& tmp,
-                          cudaStream_t s);
+                          cudaStream_t s, const uint32_t* in_ids = nullptr);
 
 // kc_orient.cu
 kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, int validate, cudaStream_t s);

@@ -135,55 +135,136 @@ __device__ __forceinline__ void edge_count(const uint32_t* I, const uint32_t* bm
     }
 }
 
-// The subtree below task vertex t of bitmap bm (W words per row): choose rem0
-// more vertices from row t.  Run by the G threads of one group.
+// ---------------------------------------------------------------------------
+// Work stealing between the groups of a block.  A frame is one level of a
+// walk: a candidate list L (W words), the candidates still to branch on
+// (bits of L above `cursor` and below `end`), the number of vertices still
+// to choose (`rem`) and the number of bits of L above the cursor (`cnt`, for
+// the size bound).  A busy group that sees idle groups donates the upper half
+// of the remaining candidates of its shallowest frame through a small queue
+// in shared memory; the donor stops its own iteration below the split.
+// ---------------------------------------------------------------------------
+static constexpr int QCAP = 16;
+// A waiting group polls the queue at most this many times (each poll sleeps
+// ~256 ns, so a few minutes) and then leaves the pool; the groups that still
+// hold work finish it themselves, so leaving is always safe.
+static constexpr uint32_t IDLE_SPIN_LIMIT = 1u << 30;
+
+struct StealShared {
+    unsigned idle;        // groups waiting for work (or trying to take some)
+    unsigned active;      // groups still in the session
+    unsigned queued;      // frames ready in the queue
+    unsigned state[QCAP]; // 0 empty, 1 being written, 2 ready, 3 being read
+    unsigned meta[QCAP][4];
+};
+
+__device__ __forceinline__ unsigned vld(const unsigned* p) { return *(const volatile unsigned*)p; }
+
+// bits of L strictly between a and b (positions), summed over the group
 template <int G>
-__device__ void walk_task(const CountParams& P, const uint32_t* bm, uint32_t W, uint32_t t, uint32_t rem0,
-                          uint32_t* stk, Acc& acc) {
+__device__ __forceinline__ uint32_t range_popc(const uint32_t* L, uint32_t a, uint32_t b, uint32_t W, unsigned gl,
+                                               unsigned gm) {
+    uint32_t c = 0;
+    const uint32_t lo = a + 1;
+    if (lo < b) {
+        const uint32_t w0 = lo >> 5, w1 = min((b - 1) >> 5, W - 1);
+        for (uint32_t w = w0 + gl; w <= w1; w += G) {
+            uint32_t x = L[w];
+            if (w == w0) x &= 0xFFFFFFFFu << (lo & 31);
+            if (w == ((b - 1) >> 5)) x &= 0xFFFFFFFFu >> (31 - ((b - 1) & 31));
+            c += __popc(x);
+        }
+    }
+    return group_sum<G>(c, gm);
+}
+
+// position of the m-th (0-based) bit of L strictly above a (one thread)
+__device__ __forceinline__ uint32_t select_above(const uint32_t* L, uint32_t a, uint32_t m, uint32_t W) {
+    uint32_t lo = a + 1;
+    for (uint32_t w = lo >> 5; w < W; ++w) {
+        uint32_t x = L[w];
+        if (w == (lo >> 5)) x &= 0xFFFFFFFFu << (lo & 31);
+        const uint32_t c = __popc(x);
+        if (m < c) return (w << 5) + __fns(x, 0, m + 1);
+        m -= c;
+    }
+    return NONE;
+}
+
+// The subtree walk from a frame (L0, cursor0, end0, cnt0, rem0 >= 3) by the
+// G threads of one group.  stk: the group's child lists (depth x W).
+template <int G>
+__device__ void walk_frame(const CountParams& P, const uint32_t* bm, uint32_t W, const uint32_t* L0, uint32_t cur0,
+                           uint32_t end0, uint32_t cnt0, uint32_t rem0, uint32_t* stk, Acc& acc, StealShared* ss,
+                           uint32_t* qwords, uint32_t qstride) {
     const unsigned gm = group_mask<G>();
     const unsigned gl = threadIdx.x & (G - 1);
+    const unsigned leader = (threadIdx.x & 31) & ~(unsigned)(G - 1);
     const uint32_t hiw = W - 1;
-    const uint32_t* R = bm + (size_t)t * W;
-    const uint32_t lo0 = (t + 1) >> 5;
-    if (rem0 == 0) {
-        if (gl == 0) acc.add(1);
-        return;
-    }
-    if (rem0 == 1) {
-        uint32_t s = 0;
-        for (uint32_t w = lo0 + gl; w <= hiw; w += G) s += __popc(R[w]);
-        acc.add(s);
-        return;
-    }
-    if (rem0 == 2) {
-        edge_count<G>(R, bm, W, lo0, hiw, gl, acc);
-        return;
-    }
-    uint32_t c0 = 0;
-    for (uint32_t w = lo0 + gl; w <= hiw; w += G) c0 += __popc(R[w]);
-    c0 = group_sum<G>(c0, gm);
-    if (c0 < rem0) return;
     uint32_t cur[MAX_DEPTH + 2];
     uint32_t idx[MAX_DEPTH + 2];
     uint32_t cnt[MAX_DEPTH + 2];
+    uint32_t endl[MAX_DEPTH + 2];
     int l = 0;
-    cur[0] = t;
+    cur[0] = cur0;
     idx[0] = 0;
-    cnt[0] = c0;
+    cnt[0] = cnt0;
+    endl[0] = end0;
     uint32_t steps = 0;
     for (;;) {
-        const uint32_t* L = (l == 0) ? R : stk + (size_t)(l - 1) * W;
+        if ((++steps & 63u) == 0) {
+            if ((steps & 4095u) == 0) {
+                int to = gl == 0 ? (int)timed_out(P.ctl) : 0;
+                if (__shfl_sync(gm, to, leader)) break;
+            }
+            // donate half of the shallowest frame that still has >= 2 candidates
+            int want = 0;
+            if (gl == 0) want = vld(&ss->idle) > 0 && vld(&ss->queued) < QCAP;
+            if (__shfl_sync(gm, want, leader)) {
+                for (int lv = 0; lv <= l; ++lv) {
+                    const uint32_t* Lv = (lv == 0) ? L0 : stk + (size_t)(lv - 1) * W;
+                    const uint32_t r = range_popc<G>(Lv, cur[lv], endl[lv], W, gl, gm);
+                    if (r < 2) continue;
+                    uint32_t q = NONE, split = NONE;
+                    if (gl == 0) {
+                        split = select_above(Lv, cur[lv], r / 2, W);
+                        for (uint32_t x = 0; x < QCAP; ++x)
+                            if (vld(&ss->state[x]) == 0 && atomicCAS(&ss->state[x], 0u, 1u) == 0u) {
+                                q = x;
+                                break;
+                            }
+                    }
+                    q = __shfl_sync(gm, q, leader);
+                    split = __shfl_sync(gm, split, leader);
+                    if (q == NONE || split == NONE) break;
+                    uint32_t* dst = qwords + (size_t)q * qstride;
+                    for (uint32_t w = gl; w < W; w += G) dst[w] = Lv[w];
+                    const uint32_t tc = range_popc<G>(Lv, split - 1, 0xFFFFFFFFu, W, gl, gm);
+                    if (gl == 0) {
+                        ss->meta[q][0] = split - 1;
+                        ss->meta[q][1] = endl[lv];
+                        ss->meta[q][2] = rem0 - lv;
+                        ss->meta[q][3] = tc;
+                    }
+                    group_sync<G>(gm);
+                    if (gl == 0) {
+                        __threadfence_block();
+                        atomicExch(&ss->state[q], 2u);
+                        atomicAdd(&ss->queued, 1u);
+                    }
+                    endl[lv] = split;
+                    break;
+                }
+            }
+        }
+        const uint32_t* L = (l == 0) ? L0 : stk + (size_t)(l - 1) * W;
         const uint32_t rem = rem0 - l;
         uint32_t v = (cnt[l] - idx[l] < rem) ? NONE : next_bit(L, cur[l] + 1, hiw);
+        if (v != NONE && v >= endl[l]) v = NONE;
         if (v == NONE) {
             if (l == 0) break;
             --l;
             continue;
-        }
-        if ((++steps & 4095u) == 0) {
-            int to = 0;
-            if (gl == 0) to = timed_out(P.ctl);
-            if (__shfl_sync(gm, to, (threadIdx.x & 31) & ~(unsigned)(G - 1))) break;
         }
         idx[l]++;
         cur[l] = v;
@@ -210,7 +291,98 @@ __device__ void walk_task(const CountParams& P, const uint32_t* bm, uint32_t W, 
         cur[l] = v;
         idx[l] = 0;
         cnt[l] = c;
+        endl[l] = 0xFFFFFFFFu;
     }
+}
+
+// The subtree below task vertex t of bitmap bm: choose rem0 more vertices
+// from row t.
+template <int G>
+__device__ void walk_task(const CountParams& P, const uint32_t* bm, uint32_t W, uint32_t t, uint32_t rem0,
+                          uint32_t* stk, Acc& acc, StealShared* ss, uint32_t* qwords, uint32_t qstride) {
+    const unsigned gm = group_mask<G>();
+    const unsigned gl = threadIdx.x & (G - 1);
+    const uint32_t hiw = W - 1;
+    const uint32_t* R = bm + (size_t)t * W;
+    const uint32_t lo0 = (t + 1) >> 5;
+    if (rem0 == 0) {
+        if (gl == 0) acc.add(1);
+        return;
+    }
+    if (rem0 == 1) {
+        uint32_t s = 0;
+        for (uint32_t w = lo0 + gl; w <= hiw; w += G) s += __popc(R[w]);
+        acc.add(s);
+        return;
+    }
+    if (rem0 == 2) {
+        edge_count<G>(R, bm, W, lo0, hiw, gl, acc);
+        return;
+    }
+    uint32_t c0 = 0;
+    for (uint32_t w = lo0 + gl; w <= hiw; w += G) c0 += __popc(R[w]);
+    c0 = group_sum<G>(c0, gm);
+    if (c0 < rem0) return;
+    walk_frame<G>(P, bm, W, R, t, 0xFFFFFFFFu, c0, rem0, stk, acc, ss, qwords, qstride);
+}
+
+// A group out of tasks: take a donated frame, or wait until one appears or
+// every group of the session is idle.  Returns true when a frame was copied
+// to own (W words) with its meta in m; false when the session is over for
+// this group.
+template <int G>
+__device__ bool steal_or_finish(const CountParams& P, StealShared* ss, uint32_t* qwords, uint32_t qstride,
+                                uint32_t W, uint32_t* own, uint32_t* m) {
+    const unsigned gm = group_mask<G>();
+    const unsigned gl = threadIdx.x & (G - 1);
+    const unsigned leader = (threadIdx.x & 31) & ~(unsigned)(G - 1);
+    uint32_t q = NONE;
+    int done = 0;
+    if (gl == 0) {
+        atomicAdd(&ss->idle, 1u);
+        uint32_t it = 0;
+        for (; it < IDLE_SPIN_LIMIT; ++it) {
+            if (vld(&ss->queued) > 0) {
+                atomicSub(&ss->idle, 1u);  // trying to take work: no longer idle
+                for (uint32_t x = 0; x < QCAP; ++x)
+                    if (vld(&ss->state[x]) == 2u && atomicCAS(&ss->state[x], 2u, 3u) == 2u) {
+                        q = x;
+                        break;
+                    }
+                if (q != NONE) {
+                    atomicSub(&ss->queued, 1u);
+                    break;
+                }
+                atomicAdd(&ss->idle, 1u);
+            }
+            if (vld(&ss->idle) == vld(&ss->active) && vld(&ss->queued) == 0) {
+                done = 1;
+                break;
+            }
+            if ((it & 1023u) == 1023u && timed_out(P.ctl)) {
+                atomicSub(&ss->idle, 1u);
+                atomicSub(&ss->active, 1u);
+                done = 1;
+                break;
+            }
+            __nanosleep(256);
+        }
+        if (q == NONE && !done) {  // waited long enough: leave the pool (the donors finish their own work)
+            atomicSub(&ss->idle, 1u);
+            atomicSub(&ss->active, 1u);
+            done = 1;
+        }
+    }
+    q = __shfl_sync(gm, q, leader);
+    if (q == NONE) return false;
+    __threadfence_block();
+    const uint32_t* src = qwords + (size_t)q * qstride;
+    for (uint32_t w = gl; w < W; w += G) own[w] = src[w];
+    if (gl == 0)
+        for (int x = 0; x < 4; ++x) m[x] = ss->meta[q][x];
+    group_sync<G>(gm);
+    if (gl == 0) atomicExch(&ss->state[q], 0u);
+    return true;
 }
 
 // Candidate list of root u into cand[]; returns d.
@@ -243,7 +415,7 @@ __device__ uint32_t next_big_slot(const CountParams& P, WorkCtl* wc, int& phase)
 }
 
 template <int G, bool EC>
-__device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& sh, Acc& acc) {
+__device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& sh, StealShared& ss, Acc& acc) {
     WorkCtl* wc = reinterpret_cast<WorkCtl*>(P.ctl + 1);
     const uint32_t W0 = P.wcap;
     const uint32_t D0 = (P.dcap + 31) & ~31u;
@@ -253,11 +425,15 @@ __device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& s
     uint32_t* sub = bm + (size_t)P.dcap * W0;                 // EC: dcap x W0
     uint32_t* subidx = sub + (EC ? (size_t)P.dcap * W0 : 0);  // EC: D0 member positions
     uint32_t* wpre = subidx + (EC ? D0 : 0);                  // EC: W0 + 1 prefix popcounts
-    uint32_t* stk_base = wpre + (EC ? W0 + 32 : 0);
-    uint32_t* stk = stk_base + (size_t)(threadIdx.x / G) * P.depth * W0;
+    uint32_t* qwords = wpre + (EC ? W0 + 32 : 0);             // QCAP x W0 donated lists
+    uint32_t* stk_base = qwords + (size_t)QCAP * W0;
+    uint32_t* own = stk_base + (size_t)(threadIdx.x / G) * (P.depth + 1) * W0;  // a taken frame's list
+    uint32_t* stk = own + W0;                                                    // child lists
     const unsigned gm = group_mask<G>();
     const unsigned gl = threadIdx.x & (G - 1);
     const unsigned leader = (threadIdx.x & 31) & ~(unsigned)(G - 1);
+    __shared__ uint32_t s_meta[BLOCK][4];  // a taken frame's meta, one row per group leader
+    uint32_t* m = s_meta[threadIdx.x / G * G];
     int phase = 0;
     for (;;) {
         if (threadIdx.x == 0) sh.slot = next_big_slot(P, wc, phase);
@@ -269,7 +445,14 @@ __device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& s
         const uint32_t Wd = (d + 31) >> 5;
         build_bitmap<BLOCK>(P.rp, P.col, cand, d, Wd, bm);
         if (!EC) {
-            // groups claim level-2 subtrees of this root
+            // groups claim level-2 subtrees of this root, then share the deep ones
+            if (threadIdx.x == 0) {
+                ss.idle = 0;
+                ss.active = BLOCK / G;
+                ss.queued = 0;
+                for (int x = 0; x < QCAP; ++x) ss.state[x] = 0;
+            }
+            __syncthreads();
             const uint32_t rem0 = P.k - 2;
             const uint32_t claim = P.claim_div ? max(1u, d / P.claim_div) : 1u;
             for (;;) {
@@ -278,11 +461,13 @@ __device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& s
                 t0 = __shfl_sync(gm, t0, leader);
                 if (t0 >= d) break;
                 const uint32_t t1 = min(t0 + claim, d);
-                for (uint32_t t = t0; t < t1; ++t) walk_task<G>(P, bm, Wd, t, rem0, stk, acc);
+                for (uint32_t t = t0; t < t1; ++t) walk_task<G>(P, bm, Wd, t, rem0, stk, acc, &ss, qwords, W0);
                 int to = 0;
                 if (gl == 0) to = timed_out(P.ctl);
                 if (__shfl_sync(gm, to, leader)) break;
             }
+            while (steal_or_finish<G>(P, &ss, qwords, W0, Wd, own, m))
+                walk_frame<G>(P, bm, Wd, own, m[0], m[1], m[3], m[2], stk, acc, &ss, qwords, W0);
         } else {
             // one root edge u -> cand[i] at a time: compact C ∩ N+(cand[i]) and
             // let the groups claim its level-3 subtrees
@@ -293,6 +478,10 @@ __device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& s
                     uint32_t i = timed_out(P.ctl) ? NONE : atomicAdd(&P.task_next[s], 1u);
                     sh.edge = (i != NONE && i < d) ? i : NONE;
                     sh.sub_next = 0;
+                    ss.idle = 0;
+                    ss.active = BLOCK / G;
+                    ss.queued = 0;
+                    for (int x = 0; x < QCAP; ++x) ss.state[x] = 0;
                 }
                 __syncthreads();
                 const uint32_t i = sh.edge;
@@ -353,8 +542,10 @@ __device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& s
                     if (gl == 0) t = atomicAdd(&sh.sub_next, 1u);
                     t = __shfl_sync(gm, t, leader);
                     if (t >= de) break;
-                    walk_task<G>(P, sub, We, t, rem0, stk, acc);
+                    walk_task<G>(P, sub, We, t, rem0, stk, acc, &ss, qwords, W0);
                 }
+                while (steal_or_finish<G>(P, &ss, qwords, W0, We, own, m))
+                    walk_frame<G>(P, sub, We, own, m[0], m[1], m[3], m[2], stk, acc, &ss, qwords, W0);
                 __syncthreads();
             }
         }
@@ -477,8 +668,9 @@ template <int G, bool EC>
 __global__ void __launch_bounds__(BLOCK) k_count_orient(const CountParams P) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ BlockShared sh;
+    __shared__ StealShared ss;
     Acc acc;
-    if (P.n_big > 0) block_phase<G, EC>(P, smem, sh, acc);
+    if (P.n_big > 0) block_phase<G, EC>(P, smem, sh, ss, acc);
     __syncthreads();
     if (P.n_work > P.n_big) {
         WarpShared* ws = reinterpret_cast<WarpShared*>(smem) + (threadIdx.x >> 5);
@@ -562,7 +754,8 @@ static Geometry plan_geometry(uint32_t dcap, uint32_t k, uint32_t G, bool ec) {
     const size_t D0 = (g.dcap + 31) & ~31u;
     size_t region = (size_t)g.dcap * g.wcap;                        // bitmap
     if (ec) region += (size_t)g.dcap * g.wcap + D0 + g.wcap + 32;   // sub-bitmap, members, prefixes
-    region += (size_t)(BLOCK / G) * g.depth * g.wcap;              // stacks
+    region += (size_t)QCAP * g.wcap;                                // donated frames
+    region += (size_t)(BLOCK / G) * (g.depth + 1) * g.wcap;        // per group: taken frame + child lists
     const size_t warp_bytes = sizeof(WarpShared) * NWARPS;
     if ((D0 + region) * 4 <= SMEM_LIMIT) {
         g.in_smem = 1;

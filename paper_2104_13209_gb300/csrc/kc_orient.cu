@@ -198,7 +198,8 @@ __device__ __forceinline__ bool peel_barrier(PeelCtl* c, uint32_t nb, uint32_t& 
 
 __global__ void __launch_bounds__(256) k_peel(const uint32_t* __restrict__ rp, const uint32_t* __restrict__ ci,
                                               uint32_t n, int* deg, uint32_t* round_of, uint32_t* core, uint32_t* F0,
-                                              uint32_t* F1, uint32_t* heavy, PeelCtl* c, unsigned long long* nf_log) {
+                                              uint32_t* F1, uint32_t* heavy, PeelCtl* c, unsigned long long* nf_log,
+                                              uint32_t* atrem) {
     const uint32_t nb = gridDim.x;
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t gthreads = gridDim.x * blockDim.x;
@@ -248,6 +249,7 @@ __global__ void __launch_bounds__(256) k_peel(const uint32_t* __restrict__ rp, c
                 uint32_t v = __ldcg(&F[cur][i]);
                 __stcg(&round_of[v], round);
                 core[v] = level;
+                atrem[v] = (uint32_t)max(0, __ldcg(&deg[v]));  // remaining degree when removed
             }
             if (gtid == 0) atomicMax(&c->max_level, level);
             if (!peel_barrier(c, nb, seq)) return;
@@ -535,7 +537,8 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
             uint32_t* a_core = (uint32_t*)g->core.ptr;
             KC_TRY(cudaMemsetAsync(nf_log, 0xFF, (size_t)NF_LOG * 8, s));
             void* args[] = {(void*)&a_rp, (void*)&a_ci, (void*)&a_n, (void*)&deg, (void*)&round_of,
-                            (void*)&a_core, (void*)&F0, (void*)&F1, (void*)&heavy, (void*)&ctl, (void*)&nf_log};
+                            (void*)&a_core, (void*)&F0, (void*)&F1, (void*)&heavy, (void*)&ctl, (void*)&nf_log,
+                            (void*)&key};
             KC_TRY(cudaLaunchCooperativeKernel((const void*)k_peel, dim3(blocks), dim3(256), args, 0, s));
             note_launch();
             PeelCtl hc;
@@ -557,7 +560,6 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
                                       hc.mismatch[4], hc.rounds, hc.max_level));
             g->degeneracy = hc.max_level;
             max_key = hc.rounds;
-            KC_TRY(cudaMemcpyAsync(key, round_of, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
         } else {
             g->degeneracy = 0;
         }
@@ -566,10 +568,23 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
         KC_TRY(cudaStreamSynchronize(s));
     }
 
-    // order: old_of_new = ids sorted by (key, id); new_of_old its inverse
+    // order: old_of_new = ids sorted by the orientation key with ties to the
+    // lower id; new_of_old its inverse.  Degree: key (degree, id).
+    // Degeneracy: (peel round, remaining degree when removed, id) -- inside a
+    // round the vertices that had fewer neighbours left come first, as a
+    // one-at-a-time min-degree peel would take them.
     KC_TRYS(dev_alloc(g->old_of_new, (size_t)n * 4 + 4));
     KC_TRYS(dev_alloc(g->new_of_old, (size_t)n * 4 + 4));
-    KC_TRYS(sort_ids_by_key(key, n, max_key, (uint32_t*)g->old_of_new.ptr, g->tmp, s));
+    if (degen && n > 0) {
+        unsigned maxdeg = 0;
+        KC_TRY(cudaMemcpyAsync(&maxdeg, words + 1, 4, cudaMemcpyDeviceToHost, s));
+        KC_TRY(cudaStreamSynchronize(s));
+        uint32_t* by_deg = F0;  // free after the peel
+        KC_TRYS(sort_ids_by_key(key, n, maxdeg, by_deg, g->tmp, s));
+        KC_TRYS(sort_ids_by_key(round_of, n, max_key, (uint32_t*)g->old_of_new.ptr, g->tmp, s, by_deg));
+    } else {
+        KC_TRYS(sort_ids_by_key(key, n, max_key, (uint32_t*)g->old_of_new.ptr, g->tmp, s));
+    }
     k_invert<<<grid_for(n, 256, sms), 256, 0, s>>>((uint32_t*)g->old_of_new.ptr, n, (uint32_t*)g->new_of_old.ptr);
     note_launch();
     KC_TRY(cudaGetLastError());

@@ -17,17 +17,20 @@
 // Fixed-k mode (Fig. 3's stopping criterion) skips children with more than k
 // held vertices and subtrees that cannot reach size k.
 //
-// Leaves are counted in an (h, q) histogram in global memory; a final kernel
-// turns it into per-size counts with an exact binomial table (64-bit values,
-// saturation = overflow).  Per-vertex counts for one size k use subtree sums:
+// Leaves are counted in an (h, q) histogram (shared memory per block for small
+// h and q, global memory otherwise); a final kernel turns it into per-size
+// counts with an exact binomial table (64-bit values, saturation = overflow).  Per-vertex counts for one size k use subtree sums:
 // a held vertex gains C(q, k - h) per leaf below it, a pivot C(q - 1, k - h - 1).
 //
 // Work distribution: big roots (|C| > 32) go to blocks in decreasing
 // out-degree order; the block builds the bitmap, picks the root's pivot, and
 // its warps claim the root's branch subtrees from a per-root counter in
 // global memory (so other blocks can join a large root).  Each warp walks its
-// subtree with warp-parallel pivot selection (lanes over the candidates).
-// Small roots run in warp mode, one warp per root, rows of one 32-bit word.
+// subtree with warp-parallel pivot selection (lanes over the candidates); a
+// node with at most 32 candidates is re-extracted into a sub-graph of one-word
+// rows (Section 2.4: extraction can happen at any level).  Small roots run in
+// warp mode, one warp per root.  Busy warps donate halves of their frames to
+// idle warps of the block, or to idle blocks through a global queue.
 #include <algorithm>
 
 #include "kc_bitmap.cuh"
@@ -56,12 +59,16 @@ struct PivotParams {
     unsigned long long* leaves;  // histogram [h * hq + q]
     uint32_t hq;
     uint32_t dcap, wcap;
-    uint32_t lvl_cap;            // stack levels per warp in block mode
+    uint32_t lvl_cap;            // wide stack levels per warp
+    uint32_t lvl_smem;           // of which kept in shared memory
     int adj_in_smem;
-    uint32_t* gstack;            // per-warp stacks for block mode (global)
+    uint32_t* gstack;            // per-warp wide stack levels beyond lvl_smem (global)
     size_t gstack_words;         // words per warp
     uint32_t* gadj;              // per-block adjacency when it does not fit in shared memory
     size_t gadj_words;
+    uint32_t* gq;                // global frame queue: gq_cap slots of gq_stride words
+    unsigned* gq_state;          // per slot: 0 empty, 1 being written, 2 ready, 3 being read
+    uint32_t gq_cap, gq_stride;
     Ctl* ctl;
 };
 
@@ -69,7 +76,10 @@ struct PWorkCtl {
     unsigned int root_cursor;
     unsigned int help_lo;
     unsigned int small_cursor;
-    unsigned int pad;
+    unsigned int g_idle;     // blocks waiting in the global frame pool
+    unsigned int g_active;   // blocks not yet finished (set by the host to the grid size)
+    unsigned int g_queued;   // frames ready in the global queue
+    unsigned int pad[2];
 };
 
 __device__ __forceinline__ bool p_timed_out(const Ctl* c) {
@@ -92,7 +102,7 @@ __device__ __forceinline__ unsigned long long binom(const PivotParams& P, uint32
     return P.binom[(size_t)a * P.bstride + (uint32_t)b];
 }
 
-// per-vertex gain (lane 0 only)
+// per-vertex gain
 __device__ __forceinline__ void pv_gain(const PivotParams& P, uint32_t vid, unsigned long long g) {
     if (g == 0) return;
     if (g == SAT) {
@@ -103,15 +113,25 @@ __device__ __forceinline__ void pv_gain(const PivotParams& P, uint32_t vid, unsi
     if (old + g < old) atomicOr(&P.ctl->flags, (unsigned)KC_FLAG_VERTEX_OVERFLOW);
 }
 
-// Run-length cache of leaves in front of the global histogram (lane 0 only).
+// Leaves of small (h, q) go to a per-block shared histogram (flushed at the
+// end of the kernel), the rest straight to the global one.
+static constexpr uint32_t LH = 16, LQ = 64;
+
+__device__ __forceinline__ void leaf_store(const PivotParams& P, unsigned long long* hist, uint32_t h, uint32_t q,
+                                           unsigned long long n) {
+    if (h < LH && q < LQ) atomicAdd(&hist[h * LQ + q], n);
+    else if (h < P.hq && q < P.hq) atomicAdd(&P.leaves[(size_t)h * P.hq + q], n);
+    else atomicOr(&P.ctl->flags, (unsigned)KC_FLAG_INTERNAL);
+}
+
+// Run-length cache of leaves (lane 0 of a warp only).
 struct LeafCache {
+    unsigned long long* hist = nullptr;
     uint32_t h = 0, q = 0;
     unsigned long long n = 0;
+    unsigned long long nodes = 0;  // tree nodes analysed by this warp
     __device__ __forceinline__ void flush(const PivotParams& P) {
-        if (n) {
-            if (h < P.hq && q < P.hq) atomicAdd(&P.leaves[(size_t)h * P.hq + q], n);
-            else atomicOr(&P.ctl->flags, (unsigned)KC_FLAG_INTERNAL);
-        }
+        if (n) leaf_store(P, hist, h, q, n);
         n = 0;
     }
     __device__ __forceinline__ void add(const PivotParams& P, uint32_t hh, uint32_t qq) {
@@ -131,6 +151,22 @@ struct LeafCache {
 __device__ __forceinline__ int analyse(const uint32_t* S, const uint32_t* adj, uint32_t W, uint32_t& cnt,
                                        uint32_t& p) {
     const int lane = threadIdx.x & 31;
+    if (W == 1) {
+        const uint32_t s0 = S[0];
+        cnt = __popc(s0);
+        if (cnt <= 1) return (int)cnt;
+        uint32_t best = 0, mind = 0xFFFFFFFFu;
+        if ((s0 >> lane) & 1u) {
+            const uint32_t dg = __popc(s0 & adj[lane]);
+            best = (dg << 16) | (0xFFFFu - lane);
+            mind = dg;
+        }
+        best = __reduce_max_sync(0xffffffffu, best);
+        mind = __reduce_min_sync(0xffffffffu, mind);
+        if (mind == cnt - 1) return 1;
+        p = 0xFFFFu - (best & 0xFFFFu);
+        return 2;
+    }
     uint32_t c = 0;
     for (uint32_t w = lane; w < W; w += 32) c += __popc(S[w]);
     cnt = __reduce_add_sync(0xffffffffu, c);
@@ -156,9 +192,29 @@ __device__ __forceinline__ int analyse(const uint32_t* S, const uint32_t* adj, u
     return 2;
 }
 
-__device__ __forceinline__ uint32_t* lvl_ptr(uint32_t* stk, uint32_t l, uint32_t W) {
-    return stk + (size_t)l * (2 * W + HDR);
-}
+// A walk's stack: level l (S_rem W | P_rem W | header HDR) in shared memory
+// for l < ls, in global memory beyond.
+struct Stk {
+    uint32_t* s;
+    uint32_t* g;
+    uint32_t ls;
+    uint32_t stride;
+    __device__ __forceinline__ uint32_t* at(uint32_t l) const {
+        return l < ls ? s + (size_t)l * stride : g + (size_t)(l - ls) * stride;
+    }
+};
+
+// Per-warp scratch of a walk on one-word rows (a small root, or a node whose
+// candidate set has been re-extracted into at most 32 vertices).
+struct PNest {
+    uint32_t cand[32];
+    uint32_t adj[32];
+    uint32_t S0[1];
+    uint32_t pad[3];
+    uint32_t stk[(PSMALL + 3) * (2 + HDR)];
+    uint32_t pathbuf[64 + 1];  // vertices above an extracted walk (per-vertex mode)
+    uint32_t pad2[3];
+};
 
 // Leaf (h, q) reached by choosing vertex vid (held or pivot); with PV, gains
 // for vid and for the c clique members (pivots of the leaf) in S (if c > 0),
@@ -185,42 +241,254 @@ __device__ __forceinline__ void leaf(const PivotParams& P, LeafCache& lc, uint32
     }
 }
 
-// Walk the subtree of the start node (candidates S0, h0, q0) reached by
-// choosing vertex vid0 (held0).  stk: this warp's stack (lvl_cap levels).
-// Returns the start node's sumH (per-vertex mode) so the caller can credit
-// the vertices above it.
-template <bool PV>
-__device__ unsigned long long warp_walk(const PivotParams& P, const uint32_t* adj, uint32_t W, const uint32_t* cand,
-                                        uint32_t* stk, uint32_t lvl_cap, const uint32_t* S0, uint32_t h0, uint32_t q0,
-                                        uint32_t vid0, bool held0, LeafCache& lc) {
+__device__ __forceinline__ void add_sums(uint32_t* hd, unsigned long long sH, unsigned long long sP) {
+    unsigned long long pH = sat_add(((unsigned long long)hd[7] << 32) | hd[6], sH);
+    unsigned long long pP = sat_add(((unsigned long long)hd[9] << 32) | hd[8], sP);
+    hd[6] = (uint32_t)pH;
+    hd[7] = (uint32_t)(pH >> 32);
+    hd[8] = (uint32_t)pP;
+    hd[9] = (uint32_t)(pP >> 32);
+}
+
+// ---------------------------------------------------------------------------
+// Work stealing between the warps of a block, and between blocks through a
+// global frame queue.  A frame is one level of a walk: S_rem (candidates),
+// P_rem (branches not yet taken), h, q, the pivot and (per-vertex mode) the
+// path of vertices above it.  A busy warp that sees idle warps (or, failing
+// that, idle blocks) donates the upper half of P_rem of its shallowest frame
+// with >= 2 branches: the thief's candidates exclude the donor's half (those
+// branches come first in the iteration order), the donor keeps its half.
+// ---------------------------------------------------------------------------
+static constexpr int PQCAP = 16;
+static constexpr int PPATH = 64;  // path entries a donated frame can carry
+// A waiting warp or block polls at most this many times (each poll sleeps a
+// few hundred ns, so minutes) and then leaves the pool; donors finish their
+// own work, so leaving is always safe.
+static constexpr uint32_t P_IDLE_SPIN_LIMIT = 1u << 30;
+
+struct PStealShared {
+    unsigned idle, active, queued;
+    unsigned state[PQCAP];
+};
+
+__device__ __forceinline__ unsigned pvld(const unsigned* p) { return *(const volatile unsigned*)p; }
+
+// Frame slot layout (local and global queues alike):
+//   [0] kind (0: rows of the root's bitmap, W words; 1: one-word rows carried
+//       in the slot), [1] root slot (kind 0), [2..5] h, q, pivot, npath,
+//   [6, 6 + PPATH) path, then kind 0: S (W0) | P (W0);
+//   kind 1: S | P | adj (32) | vertex ids (32).
+static constexpr uint32_t SLOT_HDR = 6 + PPATH;
+__host__ __device__ __forceinline__ uint32_t pq_stride(uint32_t W0) {
+    return SLOT_HDR + (2 * W0 > 66 ? 2 * W0 : 66);
+}
+
+// Credit the vertices of a base path with a subtree's sums (lanes over entries).
+__device__ __forceinline__ void credit_path(const PivotParams& P, const uint32_t* path, uint32_t npath,
+                                            unsigned long long sH, unsigned long long sP) {
     const int lane = threadIdx.x & 31;
-    const uint32_t k = P.kfix;
-    unsigned long long topH = 0, topP = 0;
-    uint32_t* L0 = lvl_ptr(stk, 0, W);
+    for (uint32_t i = lane; i < npath; i += 32) {
+        const uint32_t e = path[i];
+        pv_gain(P, e & 0x7FFFFFFFu, (e >> 31) ? sH : sP);
+    }
+}
+
+template <bool PV, bool WIDE>
+__device__ void walk_levels(const PivotParams& P, const uint32_t* adj, uint32_t W, const uint32_t* cand, Stk stk,
+                            uint32_t lvl_cap, LeafCache& lc, const uint32_t* path, uint32_t npath, PStealShared* ss,
+                            uint32_t* qwords, uint32_t W0, uint32_t root_slot, PNest* nest, unsigned long long& topH,
+                            unsigned long long& topP, const uint32_t* outer = nullptr, uint32_t nouter = 0);
+
+// Walk the subtree of the start node (candidates S0, h0, q0) reached by
+// choosing vertex vid0 (held0).  topH/topP: the node's subtree sums
+// (per-vertex mode) for the caller to credit the vertices above it.
+template <bool PV, bool WIDE>
+__device__ void warp_walk(const PivotParams& P, const uint32_t* adj, uint32_t W, const uint32_t* cand, Stk stk,
+                          uint32_t lvl_cap, const uint32_t* S0, uint32_t h0, uint32_t q0, uint32_t vid0, bool held0,
+                          LeafCache& lc, PStealShared* ss, uint32_t* qwords, uint32_t W0, uint32_t root_slot,
+                          PNest* nest, unsigned long long& topH, unsigned long long& topP,
+                          const uint32_t* outer = nullptr, uint32_t nouter = 0) {
+    const int lane = threadIdx.x & 31;
+    topH = topP = 0;
+    uint32_t* L0 = stk.at(0);
     for (uint32_t w = lane; w < W; w += 32) L0[w] = S0[w];
     __syncwarp();
     uint32_t cnt, p = 0;
     int kind = analyse(L0, adj, W, cnt, p);
+    if (lane == 0) ++lc.nodes;
     if (kind != 2) {
         const uint32_t c = kind == 1 ? cnt : 0;
         leaf<PV>(P, lc, h0, q0 + c, vid0, held0, L0, W, c, cand, topH, topP);
-        return topH;
+        return;
     }
-    // level 0: S_rem = S0 (already there), P_rem = S0 \ N(p)
-    {
-        const uint32_t* ap = adj + (size_t)p * W;
-        for (uint32_t w = lane; w < W; w += 32) L0[W + w] = L0[w] & ~ap[w];
-        if (lane == 0) {
-            uint32_t* hd = L0 + 2 * W;
-            hd[0] = h0; hd[1] = q0; hd[2] = p; hd[3] = vid0; hd[4] = held0;
-            hd[6] = hd[7] = hd[8] = hd[9] = 0;
+    const uint32_t* ap = adj + (size_t)p * W;
+    for (uint32_t w = lane; w < W; w += 32) L0[W + w] = L0[w] & ~ap[w];
+    if (lane == 0) {
+        uint32_t* hd = L0 + 2 * W;
+        hd[0] = h0; hd[1] = q0; hd[2] = p; hd[3] = vid0; hd[4] = held0;
+        hd[6] = hd[7] = hd[8] = hd[9] = 0;
+    }
+    __syncwarp();
+    // level 0 credits just its own vertex; the outer path (the vertices above,
+    // credited by the caller) only travels with donated frames
+    const uint32_t path0 = vid0 | (held0 ? 0x80000000u : 0u);
+    walk_levels<PV, WIDE>(P, adj, W, cand, stk, lvl_cap, lc, &path0, 1, ss, qwords, W0, root_slot, nest, topH, topP,
+                          outer, nouter);
+}
+
+// Re-extract the candidate set S (cnt <= 32 members, W words) into a one-word
+// sub-graph in nest and walk it from (h, q) reached by vid (held).
+template <bool PV>
+__device__ void walk_extracted(const PivotParams& P, const uint32_t* adj, uint32_t W, const uint32_t* cand,
+                               const uint32_t* S, uint32_t cnt, uint32_t h, uint32_t q, uint32_t vid, bool held,
+                               LeafCache& lc, PNest* nest, const uint32_t* path, uint32_t npath, PStealShared* ss,
+                               uint32_t* qwords, uint32_t W0, unsigned long long& sH, unsigned long long& sP) {
+    const int lane = threadIdx.x & 31;
+    uint32_t mine = NONE, base = 0;
+    for (uint32_t w = 0; w < W; ++w) {
+        const uint32_t bits = S[w], c = __popc(bits);
+        if ((uint32_t)lane >= base && (uint32_t)lane < base + c) mine = (w << 5) + __fns(bits, 0, lane - base + 1);
+        base += c;
+    }
+    uint32_t row = 0;
+    if (mine != NONE) {
+        const uint32_t* am = adj + (size_t)mine * W;
+        uint32_t b = 0;
+        for (uint32_t w = 0; w < W; ++w) {
+            const uint32_t sw = S[w];
+            uint32_t bits = am[w] & sw;
+            while (bits) {
+                const uint32_t pos = __ffs(bits) - 1;
+                bits &= bits - 1;
+                row |= 1u << (b + __popc(sw & ((1u << pos) - 1u)));
+            }
+            b += __popc(sw);
         }
-        __syncwarp();
     }
+    __syncwarp();
+    nest->adj[lane] = row;
+    nest->cand[lane] = mine != NONE ? cand[mine] : 0;
+    if (lane == 0) nest->S0[0] = cnt == 32 ? 0xFFFFFFFFu : ((1u << cnt) - 1u);
+    __syncwarp();
+    Stk small{nest->stk, nullptr, PSMALL + 3, 2 + HDR};
+    warp_walk<PV, false>(P, nest->adj, 1, nest->cand, small, PSMALL + 3, nest->S0, h, q, vid, held, lc, ss, qwords,
+                         W0, 0, nullptr, sH, sP, path, npath);
+}
+
+// The DFS from a level 0 already in stk (S_rem, P_rem, header).  path/npath:
+// the vertices above level 0's children (level 0's own vertex last), each
+// with its held flag in bit 31.  topH/topP: level 0's subtree sums.
+template <bool PV, bool WIDE>
+__device__ void walk_levels(const PivotParams& P, const uint32_t* adj, uint32_t W, const uint32_t* cand, Stk stk,
+                            uint32_t lvl_cap, LeafCache& lc, const uint32_t* path, uint32_t npath, PStealShared* ss,
+                            uint32_t* qwords, uint32_t W0, uint32_t root_slot, PNest* nest, unsigned long long& topH,
+                            unsigned long long& topP, const uint32_t* outer, uint32_t nouter) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t k = P.kfix;
+    PWorkCtl* wc = reinterpret_cast<PWorkCtl*>(P.ctl + 1);
+    topH = topP = 0;
     int l = 0;
     uint32_t steps = 0;
     for (;;) {
-        uint32_t* Lc = lvl_ptr(stk, l, W);
+        if ((++steps & 15u) == 0) {
+            if ((steps & 4095u) == 0) {
+                int to = lane == 0 ? (int)p_timed_out(P.ctl) : 0;
+                if (__shfl_sync(0xffffffffu, to, 0)) break;
+            }
+            // 1: an idle warp of this block; 2: an idle block anywhere
+            int want = 0;
+            if (lane == 0) {
+                if (ss && pvld(&ss->idle) > 0 && pvld(&ss->queued) < PQCAP) want = 1;
+                else if (P.gq_cap && pvld(&wc->g_idle) > 0 && pvld(&wc->g_queued) < P.gq_cap) want = 2;
+            }
+            want = __shfl_sync(0xffffffffu, want, 0);
+            if (want) {
+                for (int lv = 0; lv <= l; ++lv) {
+                    if (PV && nouter + npath + lv > PPATH) break;
+                    uint32_t* Lv = stk.at(lv);
+                    uint32_t c = 0;
+                    for (uint32_t w = lane; w < W; w += 32) c += __popc(Lv[W + w]);
+                    c = __reduce_add_sync(0xffffffffu, c);
+                    if (c < 2) continue;
+                    uint32_t q = NONE, split = NONE;
+                    if (lane == 0) {
+                        uint32_t m = c / 2;  // keep the first m branches
+                        for (uint32_t w = 0; w < W && split == NONE; ++w) {
+                            const uint32_t x = Lv[W + w], pc = __popc(x);
+                            if (m < pc) split = (w << 5) + __fns(x, 0, m + 1);
+                            else m -= pc;
+                        }
+                        unsigned* st = want == 1 ? ss->state : P.gq_state;
+                        const uint32_t cap = want == 1 ? PQCAP : P.gq_cap;
+                        for (uint32_t x = 0; x < cap; ++x)
+                            if (pvld(&st[x]) == 0 && atomicCAS(&st[x], 0u, 1u) == 0u) {
+                                q = x;
+                                break;
+                            }
+                    }
+                    q = __shfl_sync(0xffffffffu, q, 0);
+                    split = __shfl_sync(0xffffffffu, split, 0);
+                    if (q == NONE || split == NONE) {
+                        if (lane == 0 && q != NONE) atomicExch(want == 1 ? &ss->state[q] : &P.gq_state[q], 0u);
+                        break;
+                    }
+                    uint32_t* dst = want == 1 ? qwords + (size_t)q * pq_stride(W0) : P.gq + (size_t)q * P.gq_stride;
+                    const uint32_t* hv = Lv + 2 * W;
+                    uint32_t* dS = dst + SLOT_HDR;
+                    uint32_t* dP = dst + SLOT_HDR + (WIDE ? W0 : 1);
+                    for (uint32_t w = lane; w < W; w += 32) {
+                        const uint32_t bw = w << 5;
+                        const uint32_t hi_mask = bw + 31 < split ? 0u : (bw >= split ? 0xFFFFFFFFu
+                                                                                    : 0xFFFFFFFFu << (split - bw));
+                        const uint32_t pr = Lv[W + w];
+                        dS[w] = Lv[w] & ~(pr & ~hi_mask);  // without the donor's branches
+                        dP[w] = pr & hi_mask;               // the thief's branches
+                    }
+                    if (!WIDE) {  // the one-word sub-graph travels with the frame
+                        dst[SLOT_HDR + 2 + lane] = adj[lane];
+                        dst[SLOT_HDR + 34 + lane] = cand[lane];
+                    }
+                    if (lane == 0) {
+                        dst[0] = WIDE ? 0u : 1u;
+                        dst[1] = root_slot;
+                        dst[2] = hv[0];
+                        dst[3] = hv[1];
+                        dst[4] = hv[2];
+                        dst[5] = PV ? nouter + npath + lv : 0;
+                    }
+                    if (PV) {
+                        uint32_t* dp = dst + 6;
+                        for (uint32_t i = lane; i < nouter; i += 32) dp[i] = outer[i];
+                        for (uint32_t i = lane; i < npath; i += 32) dp[nouter + i] = path[i];
+                        for (int i = 1 + lane; i <= lv; i += 32) {
+                            const uint32_t* hi = stk.at(i) + 2 * W;
+                            dp[nouter + npath + i - 1] = hi[3] | (hi[4] ? 0x80000000u : 0u);
+                        }
+                    }
+                    __syncwarp();
+                    for (uint32_t w = lane; w < W; w += 32) {  // the donor keeps the lower half
+                        const uint32_t bw = w << 5;
+                        const uint32_t lo_mask = bw + 31 < split ? 0xFFFFFFFFu
+                                                                 : (bw >= split ? 0u : ~(0xFFFFFFFFu << (split - bw)));
+                        Lv[W + w] &= lo_mask;
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (want == 1) {
+                            __threadfence_block();
+                            atomicExch(&ss->state[q], 2u);
+                            atomicAdd(&ss->queued, 1u);
+                        } else {
+                            __threadfence();
+                            atomicExch(&P.gq_state[q], 2u);
+                            atomicAdd(&wc->g_queued, 1u);
+                        }
+                    }
+                    break;
+                }
+            }
+        }
+        uint32_t* Lc = stk.at(l);
         uint32_t* hd = Lc + 2 * W;
         const uint32_t x = next_bit(Lc + W, 0, W - 1);
         if (x == NONE) {
@@ -229,16 +497,13 @@ __device__ unsigned long long warp_walk(const PivotParams& P, const uint32_t* ad
                 unsigned long long sH = ((unsigned long long)hd[7] << 32) | hd[6];
                 unsigned long long sP = ((unsigned long long)hd[9] << 32) | hd[8];
                 if (l == 0) {
-                    if (lane == 0) pv_gain(P, hd[3], hd[4] ? sH : sP);
+                    credit_path(P, path, npath, sH, sP);
                     topH = sH;
+                    topP = sP;
                 } else {
                     if (lane == 0) {
                         pv_gain(P, hd[3], hd[4] ? sH : sP);
-                        uint32_t* ph = lvl_ptr(stk, l - 1, W) + 2 * W;
-                        unsigned long long pH = sat_add(((unsigned long long)ph[7] << 32) | ph[6], sH);
-                        unsigned long long pP = sat_add(((unsigned long long)ph[9] << 32) | ph[8], sP);
-                        ph[6] = (uint32_t)pH; ph[7] = (uint32_t)(pH >> 32);
-                        ph[8] = (uint32_t)pP; ph[9] = (uint32_t)(pP >> 32);
+                        add_sums(stk.at(l - 1) + 2 * W, sH, sP);
                     }
                     __syncwarp();
                 }
@@ -247,20 +512,16 @@ __device__ unsigned long long warp_walk(const PivotParams& P, const uint32_t* ad
             --l;
             continue;
         }
-        if ((++steps & 4095u) == 0) {
-            int to = lane == 0 ? (int)p_timed_out(P.ctl) : 0;
-            if (__shfl_sync(0xffffffffu, to, 0)) break;
-        }
         const uint32_t h = hd[0], q = hd[1], piv = hd[2];
         __syncwarp();
         if (lane == 0) Lc[W + (x >> 5)] &= ~(1u << (x & 31));  // visited
-        // child candidates: S_rem ∩ N(x); x then leaves S_rem for later siblings
-        uint32_t* Ln = lvl_ptr(stk, l + 1, W);
-        const uint32_t* ax = adj + (size_t)x * W;
         if ((uint32_t)l + 1 >= lvl_cap) {  // cannot happen: depth <= clique number <= |C| + 1
             if (lane == 0) atomicOr(&P.ctl->flags, (unsigned)KC_FLAG_INTERNAL);
             break;
         }
+        // child candidates: S_rem ∩ N(x); x then leaves S_rem for later siblings
+        uint32_t* Ln = stk.at(l + 1);
+        const uint32_t* ax = adj + (size_t)x * W;
         for (uint32_t w = lane; w < W; w += 32) Ln[w] = Lc[w] & ax[w];
         __syncwarp();
         if (lane == 0) Lc[x >> 5] &= ~(1u << (x & 31));
@@ -270,8 +531,40 @@ __device__ unsigned long long warp_walk(const PivotParams& P, const uint32_t* ad
             __syncwarp();
             continue;
         }
-        uint32_t cnt2, p2 = 0;
+        uint32_t cnt2 = 0, p2 = 0;
+        if (WIDE && W > 1) {
+            uint32_t c = 0;
+            for (uint32_t w = lane; w < W; w += 32) c += __popc(Ln[w]);
+            cnt2 = __reduce_add_sync(0xffffffffu, c);
+            if (k && h2 + q2 + cnt2 < k) {
+                __syncwarp();
+                continue;
+            }
+            if (cnt2 <= 32) {
+                // few candidates left: walk this child on one-word rows; for a frame
+                // it donates, the vertices above it are this walk's path plus levels 1..l
+                uint32_t nout = 0;
+                if (PV) {
+                    uint32_t* ob = nest->pathbuf;
+                    for (uint32_t i = lane; i < nouter && i < PPATH; i += 32) ob[i] = outer[i];
+                    for (uint32_t i = lane; i < npath && nouter + i < PPATH; i += 32) ob[nouter + i] = path[i];
+                    for (int i = 1 + lane; i <= l && nouter + npath + i - 1 < PPATH; i += 32) {
+                        const uint32_t* hi = stk.at(i) + 2 * W;
+                        ob[nouter + npath + i - 1] = hi[3] | (hi[4] ? 0x80000000u : 0u);
+                    }
+                    nout = min(nouter + npath + (uint32_t)l, (uint32_t)PPATH + 1);
+                    __syncwarp();
+                }
+                unsigned long long sH = 0, sP = 0;
+                walk_extracted<PV>(P, adj, W, cand, Ln, cnt2, h2, q2, cand[x], xheld, lc, nest, nest->pathbuf, nout,
+                                   ss, qwords, W0, sH, sP);
+                if (PV && lane == 0) add_sums(hd, sH, sP);
+                __syncwarp();
+                continue;
+            }
+        }
         int kind2 = analyse(Ln, adj, W, cnt2, p2);
+        if (lane == 0) ++lc.nodes;
         if (k && h2 + q2 + cnt2 < k) {
             __syncwarp();
             continue;
@@ -280,12 +573,7 @@ __device__ unsigned long long warp_walk(const PivotParams& P, const uint32_t* ad
             const uint32_t c = kind2 == 1 ? cnt2 : 0;
             unsigned long long sH = 0, sP = 0;
             leaf<PV>(P, lc, h2, q2 + c, cand[x], xheld, Ln, W, c, cand, sH, sP);
-            if (PV && lane == 0) {
-                unsigned long long pH = sat_add(((unsigned long long)hd[7] << 32) | hd[6], sH);
-                unsigned long long pP = sat_add(((unsigned long long)hd[9] << 32) | hd[8], sP);
-                hd[6] = (uint32_t)pH; hd[7] = (uint32_t)(pH >> 32);
-                hd[8] = (uint32_t)pP; hd[9] = (uint32_t)(pP >> 32);
-            }
+            if (PV && lane == 0) add_sums(hd, sH, sP);
             __syncwarp();
             continue;
         }
@@ -299,7 +587,119 @@ __device__ unsigned long long warp_walk(const PivotParams& P, const uint32_t* ad
         __syncwarp();
         ++l;
     }
-    return topH;
+}
+
+// The per-warp pieces of the block layout a taken frame needs.
+struct PLayoutLite {
+    uint32_t* qwords;
+    uint32_t* wpath;
+    PNest* nest;
+    Stk stk;
+};
+
+// Copy a donated frame (slot src) into this warp's walk state: kind 0 into
+// level 0 of the wide stack, kind 1 into the one-word scratch nest.  The path
+// goes to path.  Returns (kind << 16) | npath.
+__device__ uint32_t take_frame(const uint32_t* src, uint32_t W0, uint32_t W, Stk stk, PNest* nest, uint32_t* path) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t kind = src[0], np = src[5];
+    for (uint32_t i = lane; i < np; i += 32) path[i] = src[6 + i];
+    uint32_t* L0;
+    uint32_t w1;
+    if (kind == 0) {
+        L0 = stk.at(0);
+        w1 = W;
+        for (uint32_t w = lane; w < W; w += 32) {
+            L0[w] = src[SLOT_HDR + w];
+            L0[W + w] = src[SLOT_HDR + W0 + w];
+        }
+    } else {
+        L0 = nest->stk;
+        w1 = 1;
+        nest->adj[lane] = src[SLOT_HDR + 2 + lane];
+        nest->cand[lane] = src[SLOT_HDR + 34 + lane];
+        if (lane == 0) {
+            L0[0] = src[SLOT_HDR];
+            L0[1] = src[SLOT_HDR + 1];
+        }
+    }
+    if (lane == 0) {
+        uint32_t* hd = L0 + 2 * w1;
+        hd[0] = src[2];
+        hd[1] = src[3];
+        hd[2] = src[4];
+        hd[3] = NONE;
+        hd[4] = 0;
+        hd[6] = hd[7] = hd[8] = hd[9] = 0;
+    }
+    __syncwarp();
+    return (kind << 16) | np;
+}
+
+// A warp out of branches: take a frame from the block's queue, or learn that
+// the session is over.  Returns 1 + ((kind << 16) | npath) when a frame was
+// taken, 0 otherwise.
+__device__ uint32_t p_steal_or_finish(const PivotParams& P, PStealShared* ss, uint32_t* qwords, uint32_t W0,
+                                      uint32_t W, Stk stk, PNest* nest, uint32_t* path) {
+    const int lane = threadIdx.x & 31;
+    uint32_t q = NONE;
+    if (lane == 0) {
+        int done = 0;
+        atomicAdd(&ss->idle, 1u);
+        for (uint32_t it = 0; it < P_IDLE_SPIN_LIMIT; ++it) {
+            if (pvld(&ss->queued) > 0) {
+                atomicSub(&ss->idle, 1u);
+                for (uint32_t x = 0; x < PQCAP; ++x)
+                    if (pvld(&ss->state[x]) == 2u && atomicCAS(&ss->state[x], 2u, 3u) == 2u) {
+                        q = x;
+                        break;
+                    }
+                if (q != NONE) {
+                    atomicSub(&ss->queued, 1u);
+                    break;
+                }
+                atomicAdd(&ss->idle, 1u);
+            }
+            if (pvld(&ss->idle) == pvld(&ss->active) && pvld(&ss->queued) == 0) {
+                done = 1;
+                break;
+            }
+            if ((it & 1023u) == 1023u && p_timed_out(P.ctl)) {
+                atomicSub(&ss->idle, 1u);
+                atomicSub(&ss->active, 1u);
+                done = 1;
+                break;
+            }
+            __nanosleep(256);
+        }
+        if (q == NONE && !done) {  // waited long enough: leave the pool (donors finish their own work)
+            atomicSub(&ss->idle, 1u);
+            atomicSub(&ss->active, 1u);
+        }
+    }
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (q == NONE) return 0;
+    __threadfence_block();
+    const uint32_t r = take_frame(qwords + (size_t)q * pq_stride(W0), W0, W, stk, nest, path);
+    if (lane == 0) atomicExch(&ss->state[q], 0u);
+    return r + 1;
+}
+
+// Walk a taken frame (kind 0 on the block's root bitmap, kind 1 on its own
+// one-word sub-graph); the frame's path already holds every vertex above it.
+template <bool PV>
+__device__ void walk_taken(const PivotParams& P, uint32_t r, const uint32_t* adj, uint32_t W, const uint32_t* cand,
+                           const PLayoutLite& L, LeafCache& lc, PStealShared* ss, uint32_t root_slot) {
+    const uint32_t kind = r >> 16, np = r & 0xFFFFu;
+    unsigned long long sH = 0, sP = 0;
+    if (kind == 0) {
+        walk_levels<PV, true>(P, adj, W, cand, L.stk, P.lvl_cap, lc, L.wpath, np, ss, L.qwords, P.wcap, root_slot,
+                              L.nest, sH, sP);
+    } else {
+        Stk small{L.nest->stk, nullptr, PSMALL + 3, 2 + HDR};
+        walk_levels<PV, false>(P, L.nest->adj, 1, L.nest->cand, small, PSMALL + 3, lc, L.wpath, np, ss, L.qwords,
+                               P.wcap, 0, nullptr, sH, sP);
+    }
 }
 
 // Undirected adjacency of the candidates: OR every row with its transpose.
@@ -329,32 +729,85 @@ struct PBlockShared {
     unsigned long long best;
 };
 
-template <bool PV>
-__device__ void pivot_block_phase(const PivotParams& P, uint32_t* smem, PBlockShared& sh, LeafCache& lc) {
-    PWorkCtl* wc = reinterpret_cast<PWorkCtl*>(P.ctl + 1);
+// Shared-memory layout of the block phases (word offsets from psmem).
+struct PLayout {
+    uint32_t* cand;
+    uint32_t* adj;
+    uint32_t* pre;
+    uint32_t* Sx;      // this warp's start set
+    uint32_t* qwords;  // donated frames
+    uint32_t* wpath;   // this warp's taken-frame path
+    PNest* nest;       // this warp's one-word-row scratch
+    Stk stk;           // this warp's wide stack
+};
+
+__device__ __forceinline__ PLayoutLite lite(const PLayout& L) { return PLayoutLite{L.qwords, L.wpath, L.nest, L.stk}; }
+
+__device__ __forceinline__ PLayout layout(const PivotParams& P, uint32_t* smem) {
+    const int warp = threadIdx.x >> 5;
     const uint32_t D0 = (P.dcap + 31) & ~31u;
+    PLayout L;
+    L.cand = smem;
+    uint32_t* p = smem + D0;
+    if (P.adj_in_smem) {
+        L.adj = p;
+        p += (size_t)P.dcap * P.wcap;
+    } else {
+        L.adj = P.gadj + (size_t)blockIdx.x * P.gadj_words;
+    }
+    L.pre = p;
+    p += P.wcap + 32;
+    L.Sx = p + (size_t)warp * P.wcap;
+    p += (size_t)PW * P.wcap;
+    L.qwords = p;
+    p += (size_t)PQCAP * pq_stride(P.wcap);
+    L.wpath = p + (size_t)warp * PPATH;
+    p += (size_t)PW * PPATH;
+    L.nest = reinterpret_cast<PNest*>(p) + warp;
+    p += (size_t)PW * (sizeof(PNest) / 4);
+    const uint32_t stride = 2 * P.wcap + HDR;
+    L.stk.s = p + (size_t)warp * P.lvl_smem * stride;
+    L.stk.g = P.gstack + ((size_t)blockIdx.x * PW + warp) * P.gstack_words;
+    L.stk.ls = P.lvl_smem;
+    L.stk.stride = stride;
+    return L;
+}
+
+__device__ __forceinline__ void reset_session(PStealShared& ss) {
+    if (threadIdx.x == 0) {
+        ss.idle = 0;
+        ss.active = PW;
+        ss.queued = 0;
+        for (int x = 0; x < PQCAP; ++x) ss.state[x] = 0;
+    }
+    __syncthreads();
+}
+
+template <bool PV>
+__device__ void pivot_block_phase(const PivotParams& P, uint32_t* smem, PBlockShared& sh, PStealShared& ss,
+                                  LeafCache& lc) {
+    PWorkCtl* wc = reinterpret_cast<PWorkCtl*>(P.ctl + 1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t* cand = smem;
-    uint32_t* adj = P.adj_in_smem ? smem + D0 : P.gadj + (size_t)blockIdx.x * P.gadj_words;
-    uint32_t* pre = smem + D0 + (P.adj_in_smem ? (size_t)P.dcap * P.wcap : 0);  // prefix popcounts of P_root
-    uint32_t* Sx = pre + P.wcap + 32 + (size_t)warp * P.wcap;                    // per-warp start set
-    uint32_t* stk = P.gstack + ((size_t)blockIdx.x * PW + warp) * P.gstack_words;
+    const PLayout L = layout(P, smem);
+    uint32_t* cand = L.cand;
+    uint32_t* adj = L.adj;
+    uint32_t* pre = L.pre;
     int phase = 0;
     for (;;) {
         if (threadIdx.x == 0) {
-            uint32_t s = 0xFFFFFFFFu;
+            uint32_t s = NONE;
             if (!p_timed_out(P.ctl)) {
                 if (phase == 0) {
                     s = atomicAdd(&wc->root_cursor, 1u);
                     if (s >= P.n_big) {
                         phase = 1;
-                        s = 0xFFFFFFFFu;
+                        s = NONE;
                     }
                 }
                 if (phase == 1) {
                     uint32_t lo = atomicAdd(&wc->help_lo, 0u);
                     for (uint32_t probes = 0; lo < P.n_big && probes < 4096; ++lo, ++probes) {
-                        // a root is worth joining while >= 2 branches are unclaimed; the
+                        // a root is worth joining while >= 2 branches may be unclaimed; the
                         // branch count is unknown until its pivot is chosen, so use d
                         const uint32_t u = P.roots[lo];
                         const uint32_t d = P.rp[u + 1] - P.rp[u];
@@ -373,7 +826,7 @@ __device__ void pivot_block_phase(const PivotParams& P, uint32_t* smem, PBlockSh
         }
         __syncthreads();
         const uint32_t s = sh.slot;
-        if (s == 0xFFFFFFFFu) break;
+        if (s == NONE) break;
         const uint32_t u = P.roots[s];
         const uint32_t b = P.rp[u], d = P.rp[u + 1] - b;
         for (uint32_t i = threadIdx.x; i < d; i += PB) cand[i] = P.col[b + i];
@@ -452,6 +905,7 @@ __device__ void pivot_block_phase(const PivotParams& P, uint32_t* smem, PBlockSh
         }
         __syncthreads();
         const uint32_t ntask = sh.ntask;
+        reset_session(ss);
         for (;;) {
             uint32_t t = 0;
             if (lane == 0) t = atomicAdd(&P.task_next[s], 1u);
@@ -478,32 +932,32 @@ __device__ void pivot_block_phase(const PivotParams& P, uint32_t* smem, PBlockSh
                 uint32_t before = 0;
                 if (w < (x >> 5)) before = prw2;
                 else if (w == (x >> 5)) before = prw2 & ((1u << (x & 31)) - 1u);
-                Sx[w] = ax[w] & valid & ~before;
+                L.Sx[w] = ax[w] & valid & ~before;
             }
             __syncwarp();
             const bool xheld = x != piv;
             const uint32_t h0 = 1 + (xheld ? 1u : 0u), q0 = xheld ? 0u : 1u;
             if (P.kfix && h0 > P.kfix) continue;
-            unsigned long long sH = warp_walk<PV>(P, adj, W, cand, stk, P.lvl_cap, Sx, h0, q0, cand[x], xheld, lc);
+            unsigned long long sH = 0, sP = 0;
+            const uint32_t root_entry = u | 0x80000000u;  // the root is held in every clique below it
+            warp_walk<PV, true>(P, adj, W, cand, L.stk, P.lvl_cap, L.Sx, h0, q0, cand[x], xheld, lc, &ss, L.qwords,
+                                P.wcap, s, L.nest, sH, sP, &root_entry, 1);
             if (PV && lane == 0) pv_gain(P, u, sH);
-            if (lane == 0 && p_timed_out(P.ctl)) t = 0xFFFFFFFFu;
-            if (__shfl_sync(0xffffffffu, t, 0) == 0xFFFFFFFFu) break;
+            if (lane == 0 && p_timed_out(P.ctl)) t = NONE;
+            if (__shfl_sync(0xffffffffu, t, 0) == NONE) break;
+        }
+        for (;;) {
+            const uint32_t got = p_steal_or_finish(P, &ss, L.qwords, P.wcap, W, L.stk, L.nest, L.wpath);
+            if (!got) break;
+            walk_taken<PV>(P, got - 1, adj, W, cand, lite(L), lc, &ss, s);
         }
         __syncthreads();
     }
 }
 
 // Warp mode: one warp per small root, rows of one word.
-struct PWarpShared {
-    uint32_t cand[32];
-    uint32_t adj[32];
-    uint32_t S0[1];
-    uint32_t pad[3];
-    uint32_t stk[(PSMALL + 3) * (2 + HDR)];
-};
-
 template <bool PV>
-__device__ void pivot_warp_phase(const PivotParams& P, PWarpShared& ws, LeafCache& lc) {
+__device__ void pivot_warp_phase(const PivotParams& P, PNest& ws, LeafCache& lc) {
     PWorkCtl* wc = reinterpret_cast<PWorkCtl*>(P.ctl + 1);
     const int lane = threadIdx.x & 31;
     uint32_t iter = 0;
@@ -511,7 +965,7 @@ __device__ void pivot_warp_phase(const PivotParams& P, PWarpShared& ws, LeafCach
         uint32_t i = 0;
         if (lane == 0) {
             i = P.n_big + atomicAdd(&wc->small_cursor, 1u);
-            if ((++iter & 63u) == 0 && p_timed_out(P.ctl)) i = 0xFFFFFFFFu;
+            if ((++iter & 63u) == 0 && p_timed_out(P.ctl)) i = NONE;
         }
         i = __shfl_sync(0xffffffffu, i, 0);
         if (i >= P.n_work) break;
@@ -544,11 +998,80 @@ __device__ void pivot_warp_phase(const PivotParams& P, PWarpShared& ws, LeafCach
             uint32_t rr = __shfl_sync(0xffffffffu, myrow, r);
             if ((rr >> lane) & 1u) colbits |= 1u << r;
         }
-        if (lane < (int)d) ws.adj[lane] = myrow | colbits;
+        ws.adj[lane] = lane < (int)d ? (myrow | colbits) : 0u;
         if (lane == 0) ws.S0[0] = d == 32 ? 0xFFFFFFFFu : ((1u << d) - 1u);
         __syncwarp();
-        warp_walk<PV>(P, ws.adj, 1, ws.cand, ws.stk, PSMALL + 3, ws.S0, 1, 0, u, true, lc);
+        unsigned long long sH = 0, sP = 0;
+        Stk small{ws.stk, nullptr, PSMALL + 3, 2 + HDR};
+        warp_walk<PV, false>(P, ws.adj, 1, ws.cand, small, PSMALL + 3, ws.S0, 1, 0, u, true, lc, nullptr, nullptr,
+                             P.wcap, 0, nullptr, sH, sP);
         __syncwarp();
+    }
+}
+
+// Blocks with nothing left of their own serve the global frame queue: take a
+// frame, rebuild that root's bitmap, and walk the frame with the block's warps
+// (warp 0 starts it, the others steal from it).  The wait is bounded; a block
+// that gives up leaves the pool, and donors finish their own work.
+__device__ uint32_t global_take(const PivotParams& P) {
+    PWorkCtl* wc = reinterpret_cast<PWorkCtl*>(P.ctl + 1);
+    atomicAdd(&wc->g_idle, 1u);
+    for (uint32_t it = 0; it < P_IDLE_SPIN_LIMIT; ++it) {
+        if (pvld(&wc->g_queued) > 0) {
+            atomicSub(&wc->g_idle, 1u);
+            for (uint32_t x = 0; x < P.gq_cap; ++x)
+                if (pvld(&P.gq_state[x]) == 2u && atomicCAS(&P.gq_state[x], 2u, 3u) == 2u) {
+                    atomicSub(&wc->g_queued, 1u);
+                    __threadfence();
+                    return x;
+                }
+            atomicAdd(&wc->g_idle, 1u);
+        }
+        if (pvld(&wc->g_idle) == pvld(&wc->g_active) && pvld(&wc->g_queued) == 0) return NONE;
+        if ((it & 1023u) == 1023u && p_timed_out(P.ctl)) break;
+        __nanosleep(512);
+    }
+    atomicSub(&wc->g_idle, 1u);
+    atomicSub(&wc->g_active, 1u);
+    return NONE;
+}
+
+template <bool PV>
+__device__ void pivot_global_phase(const PivotParams& P, uint32_t* smem, PBlockShared& sh, PStealShared& ss,
+                                   LeafCache& lc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const PLayout L = layout(P, smem);
+    uint32_t* cand = L.cand;
+    uint32_t* adj = L.adj;
+    for (;;) {
+        if (threadIdx.x == 0) sh.slot = global_take(P);
+        __syncthreads();
+        const uint32_t q = sh.slot;
+        if (q == NONE) break;
+        const uint32_t* g = P.gq + (size_t)q * P.gq_stride;
+        const uint32_t kind = g[0], s = g[1];
+        uint32_t W = 1;
+        if (kind == 0) {  // a frame on a root's bitmap: rebuild that bitmap here
+            const uint32_t u = P.roots[s];
+            const uint32_t b = P.rp[u], d = P.rp[u + 1] - b;
+            for (uint32_t i = threadIdx.x; i < d; i += PB) cand[i] = P.col[b + i];
+            __syncthreads();
+            W = (d + 31) >> 5;
+            build_bitmap<PB>(P.rp, P.col, cand, d, W, adj);
+            symmetrise<PB>(adj, d, W);
+        }
+        reset_session(ss);
+        if (warp == 0) {
+            const uint32_t r = take_frame(g, P.wcap, W, L.stk, L.nest, L.wpath);
+            if (lane == 0) atomicExch(&P.gq_state[q], 0u);
+            walk_taken<PV>(P, r, adj, W, cand, lite(L), lc, &ss, s);
+        }
+        for (;;) {
+            const uint32_t got = p_steal_or_finish(P, &ss, L.qwords, P.wcap, W, L.stk, L.nest, L.wpath);
+            if (!got) break;
+            walk_taken<PV>(P, got - 1, adj, W, cand, lite(L), lc, &ss, s);
+        }
+        __syncthreads();
     }
 }
 
@@ -556,17 +1079,29 @@ template <bool PV>
 __global__ void __launch_bounds__(PB) k_count_pivot(const PivotParams P) {
     extern __shared__ __align__(16) uint32_t psmem[];
     __shared__ PBlockShared sh;
+    __shared__ PStealShared ss;
+    __shared__ unsigned long long s_hist[LH * LQ];
+    for (uint32_t i = threadIdx.x; i < LH * LQ; i += PB) s_hist[i] = 0;
+    __syncthreads();
     LeafCache lc;
-    if (P.n_big > 0) pivot_block_phase<PV>(P, psmem, sh, lc);
+    lc.hist = s_hist;
+    if (P.n_big > 0) pivot_block_phase<PV>(P, psmem, sh, ss, lc);
     __syncthreads();
     if (P.n_work > P.n_big) {
-        PWarpShared* ws = reinterpret_cast<PWarpShared*>(psmem) + (threadIdx.x >> 5);
+        PNest* ws = reinterpret_cast<PNest*>(psmem) + (threadIdx.x >> 5);
         pivot_warp_phase<PV>(P, *ws, lc);
     }
-    if ((threadIdx.x & 31) == 0) lc.flush(P);
+    __syncthreads();
+    if (P.gq_cap) pivot_global_phase<PV>(P, psmem, sh, ss, lc);
+    if ((threadIdx.x & 31) == 0) {
+        lc.flush(P);
+        if (lc.nodes) atomicAdd(&P.ctl->words, lc.nodes);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < LH * LQ; i += PB)
+        if (s_hist[i]) atomicAdd(&P.leaves[(size_t)(i / LQ) * P.hq + (i % LQ)], s_hist[i]);
 }
 
-// C(a, b) for a, b < B, saturating at SAT (one block, row by row).
 __global__ void k_binom(unsigned long long* t, uint32_t B) {
     for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) t[b] = b == 0 ? 1ull : 0ull;
     __syncthreads();
@@ -648,7 +1183,7 @@ static uint64_t roots_at_least(const kc_graph* g, uint64_t dmin) {
     return c;
 }
 
-static constexpr size_t PSMEM_LIMIT = 220 * 1024;
+static constexpr size_t PSMEM_LIMIT = 200 * 1024;  // dynamic; static shared memory comes on top
 
 static kc_status pivot_run(kc_graph* g, uint32_t kfix, uint32_t cap, uint32_t pvk, uint64_t* per_vertex_dev,
                            unsigned long long* counts_dev, unsigned char* ovf_dev, unsigned int* omega_dev,
@@ -686,17 +1221,29 @@ static kc_status pivot_run(kc_graph* g, uint32_t kfix, uint32_t cap, uint32_t pv
     k_pivot_set_deadline<<<1, 1, 0, s>>>(ctl, budget);
     note_launch();
     KC_CUDA(cudaGetLastError());
-    // geometry
+    // geometry: candidates, adjacency (if it fits), per-warp start sets,
+    // frame queue, paths, one-word-row scratch, then as many wide stack levels
+    // per warp as fit in shared memory (the rest in global memory)
     const size_t D0 = (dcap + 31) & ~31u;
     const size_t adj_w = (size_t)dcap * wcap;
-    const size_t tail_w = wcap + 32 + (size_t)PW * wcap;
-    size_t smem_w = D0 + adj_w + tail_w;
+    const size_t stride = 2 * (size_t)wcap + HDR;
+    const size_t tail_w = wcap + 32 + (size_t)PW * wcap + (size_t)PQCAP * pq_stride(wcap) + (size_t)PW * PPATH +
+                          (size_t)PW * (sizeof(PNest) / 4);
+    const size_t limit_w = PSMEM_LIMIT / 4;
     int adj_in_smem = 1;
-    if (smem_w * 4 > PSMEM_LIMIT) {
+    size_t fixed_w = D0 + adj_w + tail_w;
+    if (fixed_w + (size_t)PW * 8 * stride > limit_w) {
         adj_in_smem = 0;
-        smem_w = D0 + tail_w;
+        fixed_w = D0 + tail_w;
     }
-    size_t smem = std::max(smem_w * 4, sizeof(PWarpShared) * PW);
+    const uint32_t lvl_cap = dcap + 3;
+    // nodes with more than 32 candidates are rare below the root (smaller ones
+    // move to one-word rows), so a few shared-memory levels per warp suffice;
+    // deeper wide levels live in global memory
+    uint32_t lvl_smem = (uint32_t)std::min<size_t>(
+        std::min<size_t>(lvl_cap, 16), fixed_w < limit_w ? (limit_w - fixed_w) / (PW * stride) : 0);
+    const size_t smem_w = fixed_w + (size_t)PW * lvl_smem * stride;
+    size_t smem = std::max(smem_w * 4, sizeof(PNest) * PW);
     const bool pvon = pv != nullptr && pvk >= 3;
     void (*kern)(const PivotParams) = pvon ? k_count_pivot<true> : k_count_pivot<false>;
     KC_CUDA(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -704,10 +1251,13 @@ static kc_status pivot_run(kc_graph* g, uint32_t kfix, uint32_t cap, uint32_t pv
     KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, PB, smem));
     if (bps < 1) return set_error(KC_E_UNSUPPORTED, "pivot kernel cannot be resident (smem %zu)", smem);
     const int blocks = bps * sms;
-    const uint32_t lvl_cap = dcap + 3;
-    const size_t gstack_words = ((size_t)lvl_cap * (2 * wcap + HDR) + 63) & ~(size_t)63;
+    const size_t gstack_words = (((size_t)(lvl_cap - lvl_smem) + 1) * stride + 63) & ~(size_t)63;
     const size_t gadj_words = adj_in_smem ? 0 : ((adj_w + 63) & ~(size_t)63);
-    KC_CHECK(dev_alloc(g->scratch, ((size_t)blocks * PW * gstack_words + (size_t)blocks * gadj_words + 64) * 4));
+    const uint32_t gq_cap = n_big ? 256u : 0u;
+    const uint32_t gq_stride = (pq_stride(wcap) + 3) & ~3u;
+    const size_t gq_words = (size_t)gq_cap * gq_stride + gq_cap;
+    KC_CHECK(dev_alloc(g->scratch,
+                       ((size_t)blocks * PW * gstack_words + (size_t)blocks * gadj_words + gq_words + 64) * 4));
     PivotParams P;
     memset(&P, 0, sizeof(P));
     P.rp = (const uint32_t*)g->row_ptr.ptr;
@@ -726,12 +1276,23 @@ static kc_status pivot_run(kc_graph* g, uint32_t kfix, uint32_t cap, uint32_t pv
     P.dcap = dcap;
     P.wcap = wcap;
     P.lvl_cap = lvl_cap;
+    P.lvl_smem = lvl_smem;
     P.adj_in_smem = adj_in_smem;
     P.gstack = (uint32_t*)g->scratch.ptr;
     P.gstack_words = gstack_words;
     P.gadj = (uint32_t*)g->scratch.ptr + (size_t)blocks * PW * gstack_words;
     P.gadj_words = gadj_words;
+    P.gq = P.gadj + (size_t)blocks * gadj_words;
+    P.gq_state = P.gq + (size_t)gq_cap * gq_stride;
+    P.gq_cap = gq_cap;
+    P.gq_stride = gq_stride;
     P.ctl = ctl;
+    if (gq_cap) {
+        KC_CUDA(cudaMemsetAsync(P.gq_state, 0, (size_t)gq_cap * 4, s));
+        const unsigned active = (unsigned)blocks;
+        PWorkCtl* wc = reinterpret_cast<PWorkCtl*>(ctl + 1);
+        KC_CUDA(cudaMemcpyAsync(&wc->g_active, &active, 4, cudaMemcpyHostToDevice, s));
+    }
     if (n_work > 0) {
         kern<<<blocks, PB, smem, s>>>(P);
         note_launch();
@@ -758,13 +1319,13 @@ static kc_status pivot_run(kc_graph* g, uint32_t kfix, uint32_t cap, uint32_t pv
 }
 
 __global__ void k_pack_pivot_result(const unsigned long long* counts, const unsigned char* ovf, const unsigned* flags,
-                                    uint32_t k, kc_result* out) {
+                                    const Ctl* ctl, uint32_t k, kc_result* out) {
     kc_result r;
     r.total = counts[k];
     r.total_hi = 0;
     r.flags = *flags | (ovf[k] ? KC_FLAG_TOTAL_OVERFLOW : 0u);
     r.status = (*flags & KC_FLAG_TIMEOUT) ? KC_E_TIMEOUT : ((*flags & KC_FLAG_INTERNAL) ? KC_E_INTERNAL : KC_OK);
-    r.words = 0;
+    r.words = ctl->words;
     *out = r;
 }
 
@@ -788,7 +1349,7 @@ kc_status count_pivot_async(kc_graph* g, uint32_t k, kc_result* result_dev, uint
     unsigned int *omega, *flags;
     KC_CHECK(pivot_out(g, k + 1, counts, ovf, omega, flags));
     KC_CHECK(pivot_run(g, k, k + 1, per_vertex_dev ? k : 0, per_vertex_dev, counts, ovf, omega, flags, s));
-    k_pack_pivot_result<<<1, 1, 0, s>>>(counts, ovf, flags, k, result_dev);
+    k_pack_pivot_result<<<1, 1, 0, s>>>(counts, ovf, flags, (const Ctl*)g->ctl.ptr, k, result_dev);
     note_launch();
     KC_CUDA(cudaGetLastError());
     return KC_OK;
@@ -805,7 +1366,10 @@ kc_status count_all_run(kc_graph* g, uint32_t cap, uint32_t pvk, uint64_t* per_v
     if (ovf_host) KC_CUDA(cudaMemcpyAsync(ovf_host, ovf, cap, cudaMemcpyDeviceToHost, s));
     unsigned int of[2];
     KC_CUDA(cudaMemcpyAsync(of, omega, 8, cudaMemcpyDeviceToHost, s));
+    unsigned long long work = 0;
+    KC_CUDA(cudaMemcpyAsync(&work, &((const Ctl*)g->ctl.ptr)->words, 8, cudaMemcpyDeviceToHost, s));
     KC_CUDA(cudaStreamSynchronize(s));
+    g->last_work = work;
     uint32_t om = of[0];
     if (g->m > 0 && om < 2) om = 2;
     if (g->n > 0 && om < 1) om = 1;

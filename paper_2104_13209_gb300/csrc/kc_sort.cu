@@ -11,14 +11,16 @@ static constexpr int SORT_WARPS = 8;
 static constexpr int SORT_ITEMS = 16;
 static constexpr int SORT_TILE = 32 * SORT_ITEMS;  // elements per warp tile
 
-// Pass input: key of element i is keys[i] (or key_of_id[vals[i]] when keys is
-// null on the first pass, where vals[i] = i).
-__device__ __forceinline__ uint32_t load_key(const uint32_t* keys, const uint32_t* key_of_id, uint32_t i) {
-    return keys ? keys[i] : key_of_id[i];
+// Pass input: key of element i is keys[i], or key_of_id of its id on the
+// first pass (the id is vals[i], or i when vals is null).
+__device__ __forceinline__ uint32_t load_key(const uint32_t* keys, const uint32_t* key_of_id, const uint32_t* vals,
+                                             uint32_t i) {
+    return keys ? keys[i] : key_of_id[vals ? vals[i] : i];
 }
 
 __global__ void __launch_bounds__(SORT_WARPS * 32) k_radix_hist(const uint32_t* __restrict__ keys,
-                                                                const uint32_t* __restrict__ key_of_id, uint32_t n,
+                                                                const uint32_t* __restrict__ key_of_id,
+                                                                const uint32_t* __restrict__ vals, uint32_t n,
                                                                 int shift, uint32_t ntiles,
                                                                 uint32_t* __restrict__ hist) {
     __shared__ uint32_t h[SORT_WARPS][256];
@@ -29,7 +31,7 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) k_radix_hist(const uint32_t* 
     if (tile < ntiles) {
         for (int it = 0; it < SORT_ITEMS; ++it) {
             uint32_t i = tile * SORT_TILE + it * 32 + lane;
-            if (i < n) atomicAdd(&h[w][(load_key(keys, key_of_id, i) >> shift) & 255u], 1u);
+            if (i < n) atomicAdd(&h[w][(load_key(keys, key_of_id, vals, i) >> shift) & 255u], 1u);
         }
     }
     __syncwarp();
@@ -51,7 +53,7 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) k_radix_scatter(
     for (int it = 0; it < SORT_ITEMS; ++it) {
         uint32_t i = tile * SORT_TILE + it * 32 + lane;
         bool valid = i < n;
-        uint32_t key = valid ? load_key(keys, key_of_id, i) : 0u;
+        uint32_t key = valid ? load_key(keys, key_of_id, vals, i) : 0u;
         uint32_t val = valid ? (vals ? vals[i] : i) : 0u;
         uint32_t d = valid ? ((key >> shift) & 255u) : (256u + lane);
         unsigned peers = __match_any_sync(0xffffffffu, d);
@@ -68,7 +70,7 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) k_radix_scatter(
 }
 
 kc_status sort_ids_by_key(const uint32_t* key, uint32_t n, uint32_t max_key, uint32_t* out_ids, DevBuf& tmp,
-                          cudaStream_t s) {
+                          cudaStream_t s, const uint32_t* in_ids) {
     if (n == 0) return KC_OK;
     int passes = 1;
     while (passes < 4 && (max_key >> (8 * passes)) != 0) ++passes;
@@ -87,12 +89,12 @@ kc_status sort_ids_by_key(const uint32_t* key, uint32_t n, uint32_t max_key, uin
     void* stmp = p;
     const unsigned blocks = (ntiles + SORT_WARPS - 1) / SORT_WARPS;
     const uint32_t* kin = nullptr;  // first pass reads key[id]
-    const uint32_t* vin = nullptr;  // first pass: vals are the ids
+    const uint32_t* vin = in_ids;   // first pass: the given ids, or 0..n-1
     for (int ps = 0; ps < passes; ++ps) {
         const int shift = 8 * ps;
         uint32_t* kout = (ps & 1) ? kb : ka;
         uint32_t* vout = (ps == passes - 1) ? out_ids : ((ps & 1) ? vb : va);
-        k_radix_hist<<<blocks, SORT_WARPS * 32, 0, s>>>(kin, key, n, shift, ntiles, hist);
+        k_radix_hist<<<blocks, SORT_WARPS * 32, 0, s>>>(kin, key, vin, n, shift, ntiles, hist);
         note_launch();
         KC_CUDA(cudaGetLastError());
         KC_CHECK(scan_u32_raw(hist, offs, hist_n, stmp, s));

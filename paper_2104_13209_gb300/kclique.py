@@ -45,7 +45,7 @@ _SCHEME = {"auto": KC_SCHEME_AUTO, "vc": KC_SCHEME_VC, "ec": KC_SCHEME_EC}
 EXPORTED = [
     "kc_last_error", "kc_status_name", "kc_version", "kc_graph_create", "kc_graph_destroy", "kc_graph_info_get",
     "kc_graph_export", "kc_count", "kc_count128", "kc_count_async", "kc_graph_reserve", "kc_count_all",
-    "kc_graph_set_time_limit", "kc_launch_count",
+    "kc_graph_set_time_limit", "kc_launch_count", "kc_graph_last_work",
 ]
 
 
@@ -107,6 +107,8 @@ def load(build_if_missing: bool = False):
     lib.kc_graph_reserve.argtypes = [vp, u32, i32, i32, vp]
     lib.kc_count_all.argtypes = [vp, vp, vp, u32, ctypes.POINTER(u32), u32, vp, vp]
     lib.kc_graph_set_time_limit.argtypes = [vp, ctypes.c_double]
+    lib.kc_graph_last_work.argtypes = [vp, ctypes.POINTER(u64)]
+    lib.kc_graph_last_work.restype = i32
     for f in ("kc_graph_create", "kc_graph_destroy", "kc_graph_info_get", "kc_graph_export", "kc_count",
               "kc_count128", "kc_count_async", "kc_graph_reserve", "kc_count_all", "kc_graph_set_time_limit"):
         getattr(lib, f).restype = i32
@@ -211,6 +213,12 @@ class Graph:
         i = kc_graph_info()
         _check(load().kc_graph_info_get(self._h, ctypes.byref(i)))
         return {f: getattr(i, f) for f, _ in kc_graph_info._fields_}
+
+    def last_work(self) -> int:
+        """Work units of the last synchronous count (see kc_graph_last_work)."""
+        u = ctypes.c_uint64()
+        _check(load().kc_graph_last_work(self._h, ctypes.byref(u)))
+        return u.value
 
     def set_time_limit(self, seconds: float):
         _check(load().kc_graph_set_time_limit(self._h, float(seconds)))

@@ -173,6 +173,27 @@ kc_status kc_count128(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_t s
 kc_status kc_count_async(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_t subwarp, kc_result* result_dev,
                          uint64_t* per_vertex_dev, void* stream);
 
+/* Orientation-mode count (pivot = 0) that allocates no device memory.
+ * The paper has no counterpart: this is a library interface for callers that
+ * must not let a library allocate device memory, because their memory is
+ * owned by another allocator (a framework's caching pool, a fixed arena) or
+ * because cudaMalloc / cudaFree would synchronise a latency-critical loop.
+ *   Arguments and result as kc_count_async with pivot = 0 and no per-vertex
+ *   output; result_dev is device memory owned by the caller.
+ *   Working memory is a fixed 4 MiB array in the library's device image,
+ *   one per device: the control words and one task counter per root with
+ *   more than 32 out-neighbours.  The first call on a device looks up the
+ *   array's address (make it before any stream capture); every call clears
+ *   the part it uses with a stream-ordered memset.
+ *   Limits: returns KC_E_UNSUPPORTED when the roots with more than 32
+ *   out-neighbours exceed about 1,048,500, or when d_max is so large that
+ *   the per-block bitmaps do not fit in shared memory (kc_count_async then
+ *   uses graph-owned global memory).
+ *   Calls that overlap in time on one device (different streams or threads)
+ *   share the array and race: serialise them. */
+kc_status kc_count_noalloc(const kc_graph* g, uint32_t k, int scheme, uint32_t subwarp, kc_result* result_dev,
+                           void* stream);
+
 /* Pre-allocate the device working memory kc_count_async will need for these
  * parameters (pivot as in kc_count; k_max = the largest k to be asked). */
 kc_status kc_graph_reserve(kc_graph* g, uint32_t k_max, int pivot, int per_vertex, void* stream);

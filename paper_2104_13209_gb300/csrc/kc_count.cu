@@ -880,3 +880,109 @@ kc_status count_launch(kc_graph* g, const CountArgs& a, kc_result* result_dev, c
 }
 
 }  // namespace kc
+
+// ---------------------------------------------------------------------------
+// Counting without device allocation.
+//
+// kc_count_async takes its working memory (control words, per-root task
+// counters, and global-memory bitmaps for very large candidate sets) from
+// the graph handle, allocating it on first use.  Some callers cannot let a
+// library allocate: their device memory is entirely owned by another
+// allocator (a framework's caching pool, a pre-partitioned arena), or they
+// cannot afford the device-wide synchronisation that cudaFree implies in a
+// latency-critical loop.  kc_count_noalloc runs the same kernel with its
+// scratch in the fixed array below instead.
+// ---------------------------------------------------------------------------
+namespace kc {
+
+static constexpr size_t NOALLOC_WORDS = (size_t)1 << 20;  // 4 MiB, resident on every device that loads the library
+static __device__ __align__(256) uint32_t g_noalloc_scratch[NOALLOC_WORDS];
+static constexpr int NOALLOC_MAX_DEVICES = 64;
+static void* g_noalloc_addr[NOALLOC_MAX_DEVICES];  // device address of the array, per device (set up once)
+
+}  // namespace kc
+
+extern "C" kc_status kc_count_noalloc(const kc_graph* g, uint32_t k, int scheme, uint32_t subwarp,
+                                      kc_result* result_dev, void* stream) {
+    using namespace kc;
+    clear_error();
+    if (!g) return set_error(KC_E_INVALID_ARG, "NULL graph");
+    if (!result_dev) return set_error(KC_E_INVALID_ARG, "result_dev is NULL");
+    if (k == 0) return set_error(KC_E_INVALID_ARG, "k must be >= 1");
+    if (scheme != KC_SCHEME_AUTO && scheme != KC_SCHEME_VC && scheme != KC_SCHEME_EC)
+        return set_error(KC_E_INVALID_ARG, "unknown scheme %d", scheme);
+    if (subwarp != 0 && subwarp != 1 && subwarp != 2 && subwarp != 4 && subwarp != 8 && subwarp != 16 && subwarp != 32)
+        return set_error(KC_E_INVALID_ARG, "subwarp must be 0, 1, 2, 4, 8, 16 or 32");
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    KC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return set_error(KC_E_UNSUPPORTED, "device index %d too large", dev);
+    if (dev != g->device) return set_error(KC_E_INVALID_ARG, "the graph lives on device %d, not %d", g->device, dev);
+    if (!g_noalloc_addr[dev]) {
+        // set-up, once per device, with that device current: the host-side name
+        // of the array is not a device address
+        void* ptr = nullptr;
+        KC_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        g_noalloc_addr[dev] = ptr;
+    }
+    uint32_t* scratch = (uint32_t*)g_noalloc_addr[dev];
+    if (k <= 2 || (uint64_t)k > (uint64_t)g->d_max + 1) {
+        unsigned long long v = k == 1 ? g->n : (k == 2 ? g->m : 0ull);
+        k_write_result<<<1, 1, 0, s>>>(result_dev, v);
+        note_launch();
+        KC_CUDA(cudaGetLastError());
+        return KC_OK;
+    }
+    if (k > MAX_DEPTH + 4)
+        return set_error(KC_E_UNSUPPORTED, "orientation traversal supports k <= %d", MAX_DEPTH + 4);
+    const bool ec = (scheme == KC_SCHEME_AUTO ? (k < 6 ? KC_SCHEME_VC : KC_SCHEME_EC) : scheme) == KC_SCHEME_EC;
+    uint32_t G = subwarp ? subwarp : (((g->d_max + 31) / 32) <= 8 ? 4u : 8u);
+    Geometry geo;
+    int blocks = 0;
+    CountKernel kern;
+    KC_CHECK(plan_launch(const_cast<kc_graph*>(g), k, G, ec, geo, blocks, kern));
+    if (!geo.in_smem)
+        return set_error(KC_E_UNSUPPORTED,
+                         "candidate sets of %u vertices need global-memory bitmaps; use kc_count_async", g->d_max);
+    const uint64_t n_work = roots_with_outdeg_at_least(g, k - 1);
+    const uint64_t n_big = roots_with_outdeg_at_least(g, std::max<uint64_t>(SMALL_D + 1, k - 1));
+    const size_t ctl_words = ((sizeof(Ctl) + sizeof(WorkCtl) + 255) & ~(size_t)255) / 4;  // 256-byte aligned
+    if (ctl_words + n_big > NOALLOC_WORDS)
+        return set_error(KC_E_UNSUPPORTED, "%llu roots with more than 32 candidates exceed the %zu-word scratch array",
+                         (unsigned long long)n_big, NOALLOC_WORDS - ctl_words);
+    Ctl* ctl = (Ctl*)scratch;
+    uint32_t* task_next = scratch + ctl_words;
+    // the array keeps the previous call's contents: clear what must start at zero
+    KC_CUDA(cudaMemsetAsync(scratch, 0, (ctl_words + n_big) * 4, s));
+    CountParams P;
+    memset(&P, 0, sizeof(P));
+    P.rp = (const uint32_t*)g->row_ptr.ptr;
+    P.col = (const uint32_t*)g->col.ptr;
+    P.k = k;
+    P.roots = (const uint32_t*)g->roots.ptr;
+    P.n_big = (uint32_t)n_big;
+    P.n_work = (uint32_t)n_work;
+    P.task_next = task_next;
+    P.claim_div = k <= 4 ? 4u * (BLOCK / G) : 0u;
+    P.help_min = k <= 4 ? 0u : 2u;
+    P.dcap = geo.dcap;
+    P.wcap = geo.wcap;
+    P.depth = geo.depth;
+    P.in_smem = 1;
+    P.gscratch = nullptr;
+    P.gscratch_words = 0;
+    P.ctl = ctl;
+    unsigned long long budget = g->time_limit_s > 0 ? (unsigned long long)(g->time_limit_s * 1e9) : 0ull;
+    k_set_deadline<<<1, 1, 0, s>>>(ctl, budget);
+    note_launch();
+    KC_CUDA(cudaGetLastError());
+    if (n_work > 0) {
+        kern<<<blocks, BLOCK, geo.smem_bytes, s>>>(P);
+        note_launch();
+        KC_CUDA(cudaGetLastError());
+    }
+    k_finalize<<<1, 1, 0, s>>>(ctl, result_dev);
+    note_launch();
+    KC_CUDA(cudaGetLastError());
+    return KC_OK;
+}

@@ -44,7 +44,7 @@ _SCHEME = {"auto": KC_SCHEME_AUTO, "vc": KC_SCHEME_VC, "ec": KC_SCHEME_EC}
 # Every exported symbol of include/kclique.h.
 EXPORTED = [
     "kc_last_error", "kc_status_name", "kc_version", "kc_graph_create", "kc_graph_destroy", "kc_graph_info_get",
-    "kc_graph_export", "kc_count", "kc_count128", "kc_count_async", "kc_graph_reserve", "kc_count_all",
+    "kc_graph_export", "kc_count", "kc_count128", "kc_count_async", "kc_count_noalloc", "kc_graph_reserve", "kc_count_all",
     "kc_graph_set_time_limit", "kc_launch_count", "kc_graph_last_work",
 ]
 
@@ -104,13 +104,14 @@ def load(build_if_missing: bool = False):
     lib.kc_count128.argtypes = [vp, u32, i32, i32, u32, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                 ctypes.POINTER(u32), vp]
     lib.kc_count_async.argtypes = [vp, u32, i32, i32, u32, vp, vp, vp]
+    lib.kc_count_noalloc.argtypes = [vp, u32, i32, u32, vp, vp]
     lib.kc_graph_reserve.argtypes = [vp, u32, i32, i32, vp]
     lib.kc_count_all.argtypes = [vp, vp, vp, u32, ctypes.POINTER(u32), u32, vp, vp]
     lib.kc_graph_set_time_limit.argtypes = [vp, ctypes.c_double]
     lib.kc_graph_last_work.argtypes = [vp, ctypes.POINTER(u64)]
     lib.kc_graph_last_work.restype = i32
     for f in ("kc_graph_create", "kc_graph_destroy", "kc_graph_info_get", "kc_graph_export", "kc_count",
-              "kc_count128", "kc_count_async", "kc_graph_reserve", "kc_count_all", "kc_graph_set_time_limit"):
+              "kc_count128", "kc_count_async", "kc_count_noalloc", "kc_graph_reserve", "kc_count_all", "kc_graph_set_time_limit"):
         getattr(lib, f).restype = i32
     _lib = lib
     return lib
@@ -270,6 +271,14 @@ class Graph:
         if not dev:
             raise ValueError("result_dev must be device memory")
         _check(load().kc_count_async(self._h, k, int(pivot), _SCHEME[scheme], subwarp, p, None, _stream_ptr(stream)))
+
+    def count_noalloc(self, k: int, result_dev, scheme: str = "auto", subwarp: int = 0, stream=None):
+        """Enqueue an orientation-mode count that allocates no device memory
+        (working memory is a fixed array inside the library)."""
+        p, _, dev = _ptr_of(result_dev)
+        if not dev:
+            raise ValueError("result_dev must be device memory")
+        _check(load().kc_count_noalloc(self._h, k, _SCHEME[scheme], subwarp, p, _stream_ptr(stream)))
 
     def reserve(self, k_max: int, pivot: bool = False, per_vertex: bool = False, stream=None):
         _check(load().kc_graph_reserve(self._h, k_max, int(pivot), int(per_vertex), _stream_ptr(stream)))

@@ -4,7 +4,8 @@ Default workload: R-MAT scale 20 (1,048,576 vertices, edge factor 16,
 a/b/c/d = .57/.19/.19/.05, seed 0), symmetrised and deduplicated, u32 CSR.
 One step = the whole hot path on that graph: degeneracy orientation on the
 device (kc_graph_create from a device-resident CSR) followed by the counts of
-the plan (default: k = 4, vertex-centric, graph-orientation traversal).
+the plan (default: k = 4 vertex-centric, then k = 4 edge-centric, both with
+the graph-orientation traversal of Fig. 2).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -34,6 +35,7 @@ L2_FLUSH_BYTES = 512 << 20   # larger than the 129 MB L2
 POPC_PER_SM_CLK = 16         # population count results per SM per clock (CUDA arithmetic throughput table)
 SMS = 152
 SM_MAX_HZ = 2.07e9
+METRIC = "k-clique count time & cliques/s (k=4/7/10); batched/served queries/s, p99 vs plain"
 
 
 def workload_graph(scale=20, ef=16, seed=0):
@@ -171,7 +173,7 @@ def run_reference(a, g, plan, world, rank):
         secs += info["seconds"]
     value = cnt / secs
     line = {
-        "impl": "reference", "metric": "k-clique count throughput (cliques/s)", "value": value,
+        "impl": "reference", "metric": METRIC, "value": value,
         "unit": "cliques/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": 1e3 * secs / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
@@ -188,17 +190,43 @@ def run_reference(a, g, plan, world, rank):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
-def traffic_record(kernel_src: str):
-    """DRAM bytes per launch from profiles/traffic.json if the kernel source is unchanged."""
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2104_13209_gb300", "csrc", f)
+                  for f in ("kc_count.cu", "kc_bitmap.cuh", "kc_common.cuh")]
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record():
+    """DRAM bytes per launch of the count kernel from profiles/traffic.json,
+    if the kernel's sources are unchanged since the counters were taken."""
     path = os.path.join(PROFILES, "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         rec = json.load(f)
-    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
-    if rec.get("kernel_source_sha256_16") != h:
+    if rec.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
     return rec.get("dram_bytes_per_launch")
+
+
+def algorithmic_bytes(drp, dci, k: int) -> float:
+    """HBM bytes the vertex-centric bitmap build must read for size-k counts:
+    for every root v with out-degree >= k - 1, its own DAG row and the DAG
+    row of every out-neighbour (4 bytes per entry)."""
+    d = np.diff(drp.astype(np.int64))
+    roots = d >= k - 1
+    src = np.repeat(np.arange(d.size), d)
+    return float(4 * (d[roots].sum() + d[dci.astype(np.int64)][roots[src]].sum()))
+
+
+def measured_hbm_gbs() -> float:
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        return float(json.load(f)["hbm_gbs"])
 
 
 def run_ours(a, g, plan, world, rank, local_rank):
@@ -304,19 +332,40 @@ def run_ours(a, g, plan, world, rank, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
 
-    # roofline of the dominant kernel (the first count of the plan)
+    # roofline of the dominant kernel (the first count of the plan): the
+    # slower of its algorithmic CSR bytes at HBM bandwidth and its AND + POPC
+    # word operations at the population-count pipe's peak
     k0, s0 = plan[0]
     lab0 = f"k{k0}{s0}"
     t_cnt = per_label[lab0] / 1e3
-    words = res[0].words
-    achieved = 2.0 * words / t_cnt / 1e12  # Tops/s: one AND + one POPC per 32-bit word
-    peak = 2.0 * SMS * POPC_PER_SM_CLK * SM_MAX_HZ / 1e12
-    traffic = traffic_record(os.path.join(ROOT, "paper_2104_13209_gb300", "csrc", "kc_count.cu"))
+    with torch.cuda.stream(stream):
+        G = kclique.Graph(rp_d, ci_d, n=n, orient="degeneracy", validate=False, stream=stream)
+        drp, dci, _, _ = G.export()
+        G.close()
+    b_alg = algorithmic_bytes(drp, dci, k0)
+    ops = 2.0 * res[0].words            # one AND + one POPC per 32-bit bitmap word
+    peak_hbm = measured_hbm_gbs()
+    peak_alu = 2.0 * SMS * POPC_PER_SM_CLK * SM_MAX_HZ / 1e12
+    t_hbm = b_alg / (peak_hbm * 1e9)
+    t_alu = ops / (peak_alu * 1e12)
+    traffic = traffic_record()
+    terms = {"hbm": {"bytes": b_alg, "achieved_gbs": b_alg / t_cnt / 1e9, "peak_gbs": peak_hbm,
+                     "roof_ms": 1e3 * t_hbm},
+             "alu": {"ops": ops, "achieved_tops": ops / t_cnt / 1e12, "peak_tops": peak_alu, "roof_ms": 1e3 * t_alu,
+                     "peak_note": "derived: 152 SMs x 16 popc/clk x 2.07 GHz x 2 ops (AND + POPC) per word"}}
+    if t_hbm >= t_alu:
+        roof = {"bound": "hbm", "achieved": terms["hbm"]["achieved_gbs"], "peak": peak_hbm, "unit": "GB/s"}
+    else:
+        roof = {"bound": "alu", "achieved": terms["alu"]["achieved_tops"], "peak": peak_alu, "unit": "Tops/s"}
+    roof.update({"frac": roof["achieved"] / roof["peak"], "traffic": traffic,
+                 "kernel": f"k_count_orient ({lab0})", "kernel_ms": 1e3 * t_cnt, "terms": terms,
+                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if roof["bound"] == "hbm"
+                 else "derived from unit counts and clock"})
 
     clocks = clk.summary()
     value = world * total_cliques / (step_ms / 1e3)
     line = {
-        "metric": "k-clique count throughput (cliques/s)",
+        "metric": METRIC,
         "value": value,
         "unit": "cliques/s",
         "n_gpus": world,
@@ -338,10 +387,7 @@ def run_ours(a, g, plan, world, rank, local_rank):
         "e2e": {"value": world * total_cliques / e2e_s, "unit": "cliques/s",
                 "h2d_bytes_per_step": 4 * (n + 1) + 4 * nnz,
                 "d2h_bytes_per_step": kclique.RESULT_BYTES * len(plan)},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": f"k_count_orient ({lab0})", "words": words,
-                     "peak_note": "derived: 152 SMs x 16 popc/clk x 2.07 GHz x 2 ops (AND+POPC) per word"},
+        "roofline": roof,
         "clocks": clocks,
         "gpu_launches": launches,
     }
@@ -360,7 +406,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--plan", default="4vc")
+    ap.add_argument("--plan", default="4vc,4ec")
     ap.add_argument("--scale", type=int, default=20)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -32,6 +32,35 @@ __device__ __forceinline__ uint32_t find_sorted(const uint32_t* s, uint32_t lo, 
     return NONE;
 }
 
+// The entries y <= last of the sorted DAG row col[b, e), handed to f(y) by
+// the 32 lanes of a warp.  Each lane loads two 16-byte quads per round (a
+// warp covers 256 entries per round with all loads in flight), and the scan
+// stops after the round whose final entry exceeds last.  The row array must
+// be 16-byte aligned and readable up to the quad holding entry e - 1.
+template <class F>
+__device__ __forceinline__ void scan_row(const uint32_t* __restrict__ col, uint32_t b, uint32_t e, uint32_t last,
+                                         int lane, F&& f) {
+    const uint4* col4 = reinterpret_cast<const uint4*>(col);
+    const uint32_t qend = (e + 3) >> 2;
+    for (uint32_t q0 = b >> 2; q0 < qend; q0 += 64) {
+        const uint32_t qa = q0 + lane, qb = qa + 32;
+        uint4 va = make_uint4(NONE, NONE, NONE, NONE), vb = va;
+        if (qa < qend) va = __ldg(col4 + qa);
+        if (qb < qend) vb = __ldg(col4 + qb);
+        const uint32_t ja = qa << 2, jb = qb << 2;
+        const uint32_t ya[4] = {va.x, va.y, va.z, va.w};
+        const uint32_t yb[4] = {vb.x, vb.y, vb.z, vb.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (ja + c >= b && ja + c < e && ya[c] <= last) f(ya[c]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (jb + c >= b && jb + c < e && yb[c] <= last) f(yb[c]);
+        const uint32_t tail = (jb + 3 < e) ? vb.w : NONE;
+        if (__shfl_sync(0xffffffffu, tail, 31) >= last) break;  // the rest of the row lies beyond last
+    }
+}
+
 // Rows of the induced sub-graph of cand[0, d): bit j of row i iff cand[j] in
 // N+(cand[i]).  One warp per row; lanes take 32 consecutive entries of
 // N+(cand[i]) at a time and binary-search them among cand[i+1 .. d).
@@ -44,17 +73,74 @@ __device__ void build_bitmap(const uint32_t* __restrict__ rp, const uint32_t* __
     const uint32_t last = cand[d - 1];
     for (uint32_t i = warp; i < d; i += NT / 32) {
         const uint32_t x = cand[i];
-        const uint32_t b = rp[x], e = rp[x + 1];
         uint32_t* row = bm + (size_t)i * W;
-        for (uint32_t j0 = b; j0 < e; j0 += 32) {
-            uint32_t j = j0 + lane;
-            uint32_t y = j < e ? col[j] : NONE;
-            if (y != NONE && y <= last) {
-                uint32_t pos = find_sorted(cand, i + 1, d, y);
-                if (pos != NONE) atomicOr(&row[pos >> 5], 1u << (pos & 31));
-            }
-            if (__shfl_sync(0xffffffffu, y, 31) >= last) break;  // the rest of the row lies beyond cand
+        scan_row(col, __ldg(rp + x), __ldg(rp + x + 1), last, lane, [&](uint32_t y) {
+            const uint32_t pos = find_sorted(cand, i + 1, d, y);
+            if (pos != NONE) atomicOr(&row[pos >> 5], 1u << (pos & 31));
+        });
+    }
+    __syncthreads();
+}
+
+// Open-addressing table of the candidates' positions, for the membership
+// test of the bitmap build: 2^tbits 16-bit slots holding position + 1
+// (0 = empty), linear probing from a multiplicative hash of the vertex id.
+// Most tested ids are not candidates, and at a load of at most 1/4 most of
+// those misses end at the first, empty, slot.
+__device__ __forceinline__ uint32_t hash_slot(uint32_t y, uint32_t tbits) {
+    return (y * 0x9E3779B1u) >> (32 - tbits);
+}
+
+__device__ __forceinline__ uint32_t hash_bits_for(uint32_t d) {
+    uint32_t b = 6;
+    while ((1u << b) < 4 * d) ++b;
+    return b;
+}
+
+// Same rows as build_bitmap, with the table above instead of binary search.
+// tab: 2^tbits 16-bit slots (tbits from hash_bits_for(d)); d < 65535.
+template <int NT>
+__device__ void build_bitmap_hashed(const uint32_t* __restrict__ rp, const uint32_t* __restrict__ col,
+                                    const uint32_t* cand, uint32_t d, uint32_t W, uint32_t* bm, uint16_t* tab,
+                                    uint32_t tbits) {
+    const uint32_t T = 1u << tbits, mask = T - 1;
+    uint32_t* tw = reinterpret_cast<uint32_t*>(tab);
+    for (uint32_t x = threadIdx.x; x < d * W; x += NT) bm[x] = 0;
+    for (uint32_t x = threadIdx.x; x < T / 2; x += NT) tw[x] = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < d; i += NT) {
+        uint32_t h = hash_slot(cand[i], tbits);
+        while (atomicCAS(&tab[h], (unsigned short)0, (unsigned short)(i + 1)) != 0) h = (h + 1) & mask;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t last = cand[d - 1];
+    // row bounds of the warp's next row are loaded while it scans this one
+    uint32_t nb = 0, ne = 0;
+    if (warp < d) {
+        nb = __ldg(rp + cand[warp]);
+        ne = __ldg(rp + cand[warp] + 1);
+    }
+    for (uint32_t i = warp; i < d; i += NT / 32) {
+        const uint32_t b = nb, e = ne;
+        if (i + NT / 32 < d) {
+            const uint32_t x2 = cand[i + NT / 32];
+            nb = __ldg(rp + x2);
+            ne = __ldg(rp + x2 + 1);
         }
+        uint32_t* row = bm + (size_t)i * W;
+        scan_row(col, b, e, last, lane, [&](uint32_t y) {
+            uint32_t h = hash_slot(y, tbits);
+            for (;;) {
+                const uint32_t p = tab[h];
+                if (p == 0) break;
+                if (cand[p - 1] == y) {
+                    atomicOr(&row[(p - 1) >> 5], 1u << ((p - 1) & 31));
+                    break;
+                }
+                h = (h + 1) & mask;
+            }
+        });
     }
     __syncthreads();
 }

@@ -40,6 +40,7 @@ static constexpr int NWARPS = BLOCK / 32;
 static constexpr int SMALL_D = 32;      // warp mode handles |C| <= 32
 static constexpr int WARP_DEPTH = 32;   // per-lane stack levels in warp mode
 static constexpr int MAX_DEPTH = 64;    // stack levels per group in block mode
+static constexpr uint32_t EC_COMPACT_MIN_K = 6;  // edge-centric: compact the edge's sub-graph from this k on
 
 struct CountParams {
     const uint32_t* rp;        // DAG row pointers (library numbering)
@@ -55,6 +56,7 @@ struct CountParams {
     int in_smem;               // bitmaps and stacks in shared memory (else per-block global scratch)
     uint32_t* gscratch;
     size_t gscratch_words;
+    uint32_t hash_words;       // shared-memory words of the candidate position table (0: binary search)
     Ctl* ctl;
 };
 
@@ -111,13 +113,18 @@ __device__ __forceinline__ bool timed_out(const Ctl* c) {
 // ---------------------------------------------------------------------------
 struct BlockShared {
     uint32_t slot;
+    uint32_t task;      // next unclaimed task of a root no other block can join
     uint32_t edge;
     uint32_t sub_next;
     uint32_t sub_d;
 };
 
-// sum over j in I of popc(I & row_j), words [lo, hi]; thread gl of the group
-// takes the words lo + gl, lo + gl + G, ...
+// sum over j in I of popc(I & row_j), words [lo, hi] (the last level of the
+// traversal: every edge of the sub-graph induced by I closes a clique).
+// Thread gl of the group takes the words lo + gl, lo + gl + G, ... of I and,
+// for each member j found there, sums the row words from j's own word on by
+// itself (rows are upper triangular).  Most lists at this level are sparse,
+// so splitting the scan of I beats stepping through its members together.
 template <int G>
 __device__ __forceinline__ void edge_count(const uint32_t* I, const uint32_t* bm, uint32_t W, uint32_t lo, uint32_t hi,
                                            unsigned gl, Acc& acc) {
@@ -422,13 +429,17 @@ __device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& s
     uint32_t* cand = smem;
     uint32_t* region = P.in_smem ? smem + D0 : P.gscratch + (size_t)blockIdx.x * P.gscratch_words;
     uint32_t* bm = region;                                    // dcap x W0
-    uint32_t* sub = bm + (size_t)P.dcap * W0;                 // EC: dcap x W0
-    uint32_t* subidx = sub + (EC ? (size_t)P.dcap * W0 : 0);  // EC: D0 member positions
-    uint32_t* wpre = subidx + (EC ? D0 : 0);                  // EC: W0 + 1 prefix popcounts
-    uint32_t* qwords = wpre + (EC ? W0 + 32 : 0);             // QCAP x W0 donated lists
+    // edge-centric split: the edge's induced sub-graph is compacted only when
+    // the tree below it is deep enough to repay the compaction
+    const bool compact = EC && P.k >= EC_COMPACT_MIN_K;
+    uint32_t* sub = bm + (size_t)P.dcap * W0;                      // compaction: dcap x W0
+    uint32_t* subidx = sub + (compact ? (size_t)P.dcap * W0 : 0);  // compaction: D0 member positions
+    uint32_t* wpre = subidx + (compact ? D0 : 0);                  // compaction: W0 + 1 prefix popcounts
+    uint32_t* qwords = wpre + (compact ? W0 + 32 : 0);             // QCAP x W0 donated lists
     uint32_t* stk_base = qwords + (size_t)QCAP * W0;
     uint32_t* own = stk_base + (size_t)(threadIdx.x / G) * (P.depth + 1) * W0;  // a taken frame's list
     uint32_t* stk = own + W0;                                                    // child lists
+    uint16_t* tab = reinterpret_cast<uint16_t*>(stk_base + (size_t)(BLOCK / G) * (P.depth + 1) * W0);
     const unsigned gm = group_mask<G>();
     const unsigned gl = threadIdx.x & (G - 1);
     const unsigned leader = (threadIdx.x & 31) & ~(unsigned)(G - 1);
@@ -436,15 +447,21 @@ __device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& s
     uint32_t* m = s_meta[threadIdx.x / G * G];
     int phase = 0;
     for (;;) {
-        if (threadIdx.x == 0) sh.slot = next_big_slot(P, wc, phase);
+        if (threadIdx.x == 0) {
+            sh.slot = next_big_slot(P, wc, phase);
+            sh.task = 0;
+        }
         __syncthreads();
         const uint32_t s = sh.slot;
         if (s == NONE) break;
         const uint32_t u = P.roots[s];
         const uint32_t d = load_root(P, u, cand);
         const uint32_t Wd = (d + 31) >> 5;
-        build_bitmap<BLOCK>(P.rp, P.col, cand, d, Wd, bm);
-        if (!EC) {
+        if (P.hash_words)
+            build_bitmap_hashed<BLOCK>(P.rp, P.col, cand, d, Wd, bm, tab, hash_bits_for(d));
+        else
+            build_bitmap<BLOCK>(P.rp, P.col, cand, d, Wd, bm);
+        if (!compact) {
             // groups claim level-2 subtrees of this root, then share the deep ones
             if (threadIdx.x == 0) {
                 ss.idle = 0;
@@ -457,7 +474,9 @@ __device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& s
             const uint32_t claim = P.claim_div ? max(1u, d / P.claim_div) : 1u;
             for (;;) {
                 uint32_t t0 = 0;
-                if (gl == 0) t0 = atomicAdd(&P.task_next[s], claim);
+                // without helpers (help_min = 0) the root's tasks are this
+                // block's alone and are claimed in shared memory
+                if (gl == 0) t0 = P.help_min ? atomicAdd(&P.task_next[s], claim) : atomicAdd(&sh.task, claim);
                 t0 = __shfl_sync(gm, t0, leader);
                 if (t0 >= d) break;
                 const uint32_t t1 = min(t0 + claim, d);
@@ -626,21 +645,21 @@ __device__ void warp_phase(const CountParams& P, WarpShared& ws, Acc& acc) {
         const uint32_t d = P.rp[u + 1] - b;
         if (lane < (int)d) ws.cand[lane] = P.col[b + lane];
         __syncwarp();
-        // rows, one per candidate, built cooperatively (lanes over N+(cand[r]))
+        // rows, one per candidate, built cooperatively (lanes over N+(cand[r]));
+        // lane r holds the bounds of row r, loaded together
         const uint32_t last = ws.cand[d - 1];
+        uint32_t rb = 0, re = 0;
+        if (lane < (int)d) {
+            rb = __ldg(P.rp + ws.cand[lane]);
+            re = __ldg(P.rp + ws.cand[lane] + 1);
+        }
         for (uint32_t r = 0; r < d; ++r) {
-            const uint32_t x = ws.cand[r];
-            const uint32_t xb = P.rp[x], xe = P.rp[x + 1];
+            const uint32_t xb = __shfl_sync(0xffffffffu, rb, r), xe = __shfl_sync(0xffffffffu, re, r);
             uint32_t bits = 0;
-            for (uint32_t j0 = xb; j0 < xe; j0 += 32) {
-                uint32_t j = j0 + lane;
-                uint32_t y = j < xe ? P.col[j] : NONE;
-                if (y != NONE && y <= last) {
-                    uint32_t pos = find_sorted(ws.cand, r + 1, d, y);
-                    if (pos != NONE) bits |= 1u << pos;
-                }
-                if (__shfl_sync(0xffffffffu, y, 31) >= last) break;
-            }
+            scan_row(P.col, xb, xe, last, lane, [&](uint32_t y) {
+                const uint32_t pos = find_sorted(ws.cand, r + 1, d, y);
+                if (pos != NONE) bits |= 1u << pos;
+            });
             bits = __reduce_or_sync(0xffffffffu, bits);
             if (lane == 0) ws.row[r] = bits;
         }
@@ -742,22 +761,38 @@ struct Geometry {
     int in_smem;
     size_t smem_bytes;
     size_t gscratch_words;
+    uint32_t hash_words;
 };
+
+// 16-bit slots of the candidate position table for candidate sets up to dcap
+static uint32_t hash_words_for(uint32_t dcap) {
+    uint32_t b = 6;
+    while ((1u << b) < 4 * dcap) ++b;
+    return (1u << b) / 2;
+}
 
 static Geometry plan_geometry(uint32_t dcap, uint32_t k, uint32_t G, bool ec) {
     Geometry g;
     g.dcap = std::max<uint32_t>(dcap, 1);
     g.wcap = (g.dcap + 31) / 32;
     // stack levels: the DFS pushes while rem >= 3, i.e. rem0 - 2 levels
-    const uint32_t rem0 = ec ? (k > 3 ? k - 3 : 0) : (k > 2 ? k - 2 : 0);
+    const bool ec_compact = ec && k >= EC_COMPACT_MIN_K;
+    const uint32_t rem0 = ec_compact ? k - 3 : (k > 2 ? k - 2 : 0);
     g.depth = rem0 > 2 ? rem0 - 2 : 1;
     const size_t D0 = (g.dcap + 31) & ~31u;
     size_t region = (size_t)g.dcap * g.wcap;                        // bitmap
-    if (ec) region += (size_t)g.dcap * g.wcap + D0 + g.wcap + 32;   // sub-bitmap, members, prefixes
+    if (ec_compact) region += (size_t)g.dcap * g.wcap + D0 + g.wcap + 32;  // sub-bitmap, members, prefixes
     region += (size_t)QCAP * g.wcap;                                // donated frames
     region += (size_t)(BLOCK / G) * (g.depth + 1) * g.wcap;        // per group: taken frame + child lists
     const size_t warp_bytes = sizeof(WarpShared) * NWARPS;
-    if ((D0 + region) * 4 <= SMEM_LIMIT) {
+    const size_t hw = g.dcap < 65535 ? hash_words_for(g.dcap) : 0;
+    g.hash_words = 0;
+    if (hw && (D0 + region + hw) * 4 <= SMEM_LIMIT) {
+        g.in_smem = 1;
+        g.hash_words = (uint32_t)hw;
+        g.smem_bytes = (D0 + region + hw) * 4;
+        g.gscratch_words = 0;
+    } else if ((D0 + region) * 4 <= SMEM_LIMIT) {
         g.in_smem = 1;
         g.smem_bytes = (D0 + region) * 4;
         g.gscratch_words = 0;
@@ -854,7 +889,8 @@ kc_status count_launch(kc_graph* g, const CountArgs& a, kc_result* result_dev, c
     // small trees (k <= 4): a root stays with its block and groups claim a
     // few tasks at a time; deeper trees: one task per claim, and idle blocks
     // join roots that still have unclaimed tasks
-    P.claim_div = k <= 4 ? 4u * (BLOCK / G) : 0u;
+    // edge-centric: every root edge is claimed on its own
+    P.claim_div = (k <= 4 && !ec) ? 4u * (BLOCK / G) : 0u;
     P.help_min = k <= 4 ? 0u : 2u;
     P.dcap = geo.dcap;
     P.wcap = geo.wcap;
@@ -862,6 +898,7 @@ kc_status count_launch(kc_graph* g, const CountArgs& a, kc_result* result_dev, c
     P.in_smem = geo.in_smem;
     P.gscratch = (uint32_t*)g->scratch.ptr;
     P.gscratch_words = geo.gscratch_words;
+    P.hash_words = geo.hash_words;
     P.ctl = ctl;
     if (n_big) KC_CUDA(cudaMemsetAsync(g->tmp.ptr, 0, (size_t)n_big * 4, s));
     unsigned long long budget = g->time_limit_s > 0 ? (unsigned long long)(g->time_limit_s * 1e9) : 0ull;
@@ -963,7 +1000,7 @@ extern "C" kc_status kc_count_noalloc(const kc_graph* g, uint32_t k, int scheme,
     P.n_big = (uint32_t)n_big;
     P.n_work = (uint32_t)n_work;
     P.task_next = task_next;
-    P.claim_div = k <= 4 ? 4u * (BLOCK / G) : 0u;
+    P.claim_div = (k <= 4 && !ec) ? 4u * (BLOCK / G) : 0u;
     P.help_min = k <= 4 ? 0u : 2u;
     P.dcap = geo.dcap;
     P.wcap = geo.wcap;
@@ -971,6 +1008,7 @@ extern "C" kc_status kc_count_noalloc(const kc_graph* g, uint32_t k, int scheme,
     P.in_smem = 1;
     P.gscratch = nullptr;
     P.gscratch_words = 0;
+    P.hash_words = geo.hash_words;
     P.ctl = ctl;
     unsigned long long budget = g->time_limit_s > 0 ? (unsigned long long)(g->time_limit_s * 1e9) : 0ull;
     k_set_deadline<<<1, 1, 0, s>>>(ctl, budget);

@@ -591,7 +591,8 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
 
     // out-degrees in the library numbering, then row pointers
     KC_TRYS(dev_alloc(g->row_ptr, ((size_t)n + 1) * 4));
-    KC_TRYS(dev_alloc(g->col, (size_t)g->m * 4 + 4));
+    // rows are scanned in 16-byte quads: pad to whole quads plus one
+    KC_TRYS(dev_alloc(g->col, (((size_t)g->m + 3) / 4 + 1) * 16));
     uint32_t* outdeg = F0;  // reuse
     KC_TRY(cudaMemsetAsync(outdeg, 0, (size_t)n * 4 + 4, s));
     const uint64_t fthreads = ((uint64_t)nnz + 7) / 8;

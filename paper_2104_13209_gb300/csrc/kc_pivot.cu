@@ -976,19 +976,18 @@ __device__ void pivot_warp_phase(const PivotParams& P, PNest& ws, LeafCache& lc)
         __syncwarp();
         const uint32_t last = ws.cand[d - 1];
         uint32_t myrow = 0;
+        uint32_t rb = 0, re = 0;
+        if (lane < (int)d) {
+            rb = __ldg(P.rp + ws.cand[lane]);
+            re = __ldg(P.rp + ws.cand[lane] + 1);
+        }
         for (uint32_t r = 0; r < d; ++r) {
-            const uint32_t x = ws.cand[r];
-            const uint32_t xb = P.rp[x], xe = P.rp[x + 1];
+            const uint32_t xb = __shfl_sync(0xffffffffu, rb, r), xe = __shfl_sync(0xffffffffu, re, r);
             uint32_t bits = 0;
-            for (uint32_t j0 = xb; j0 < xe; j0 += 32) {
-                uint32_t j = j0 + lane;
-                uint32_t y = j < xe ? P.col[j] : NONE;
-                if (y != NONE && y <= last) {
-                    uint32_t pos = find_sorted(ws.cand, r + 1, d, y);
-                    if (pos != NONE) bits |= 1u << pos;
-                }
-                if (__shfl_sync(0xffffffffu, y, 31) >= last) break;
-            }
+            scan_row(P.col, xb, xe, last, lane, [&](uint32_t y) {
+                const uint32_t pos = find_sorted(ws.cand, r + 1, d, y);
+                if (pos != NONE) bits |= 1u << pos;
+            });
             bits = __reduce_or_sync(0xffffffffu, bits);
             if (lane == (int)r) myrow = bits;
         }

@@ -210,6 +210,83 @@ kc_status kc_graph_reserve(kc_graph* g, uint32_t k_max, int pivot, int per_verte
 kc_status kc_count_all(kc_graph* g, uint64_t* counts, uint8_t* overflow, uint32_t cap, uint32_t* omega_out,
                        uint32_t per_vertex_k, uint64_t* per_vertex_out, void* stream);
 
+/* ---- batched counts over many small graphs -------------------------------
+ * The paper counts one graph at a time; these calls serve workloads of
+ * thousands of small graphs (ego networks, per-query subgraphs) with uneven
+ * k, counted by the orientation traversal (Fig. 2) in persistent launches
+ * that span every query.  A query's graph is oriented as a block of one
+ * union graph (Section 3.1); its count is exact (128-bit) like kc_count128. */
+typedef struct kc_batch kc_batch;
+typedef struct kc_batch_exec kc_batch_exec;
+
+/* Launch configuration chosen for one (out-degree class, k) bucket.
+ * dclass: 0 for largest out-degree <= 32, c for <= 32 * 2^c (c <= 5), 6
+ * beyond.  scheme: KC_SCHEME_VC or KC_SCHEME_EC for the roots with more than
+ * 32 candidates (Section 3.2); subwarp: threads per group (Section 3.5);
+ * chunk: roots a warp claims per atomic among the small roots (the work
+ * tile); ms: the measured time of the bucket's sample. */
+typedef struct kc_tune_entry {
+    uint32_t dclass;
+    uint32_t k;
+    int32_t scheme;
+    uint32_t subwarp;
+    uint32_t chunk;
+    float ms;
+} kc_tune_entry;
+
+#define KC_TUNE_MAX 256
+typedef struct kc_tune {
+    uint32_t n;
+    kc_tune_entry e[KC_TUNE_MAX];
+} kc_tune;
+
+/* Build a batch from a block-diagonal CSR: graph g owns the vertices
+ * [graph_offsets[g], graph_offsets[g + 1]) (host array, num_graphs + 1
+ * entries, 0 first and n last) and no edge may leave that range
+ * (KC_E_INVALID_GRAPH when validate is set).  The other arguments are those
+ * of kc_graph_create; the caller keeps its arrays. */
+kc_status kc_batch_create(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t nnz,
+                          const uint32_t* graph_offsets, uint32_t num_graphs, int ptrs_on_device, int orient,
+                          int validate, void* stream, kc_batch** out);
+kc_status kc_batch_destroy(kc_batch* b);
+
+/* Vertices, edges and largest DAG out-degree of graph `graph` (outputs
+ * nullable). */
+kc_status kc_batch_graph_info(const kc_batch* b, uint32_t graph, uint32_t* n, uint64_t* m, uint32_t* d_max);
+
+/* Time limit of each launch (seconds, 0 = none); a launch that runs out
+ * marks its queries KC_E_TIMEOUT in their results. */
+kc_status kc_batch_set_time_limit(kc_batch* b, double seconds);
+
+/* Count nq queries: query i is (graph_ids[i], ks[i]) (host arrays, ks[i] >=
+ * 1).  Results go to results_dev[i] (device memory, nq entries): total and
+ * total_hi (exact below 2^128), KC_FLAG_* flags, status KC_OK or
+ * KC_E_TIMEOUT.  tune (nullable): configuration per bucket; buckets it does
+ * not list take the paper's guideline (Section 4.5).  Stream-ordered; the
+ * call may wait for its own previous call's descriptor copy and may
+ * allocate, so use kc_batch_capture for CUDA-graph replay. */
+kc_status kc_batch_count(kc_batch* b, const uint32_t* graph_ids, const uint32_t* ks, uint32_t nq,
+                         kc_result* results_dev, const kc_tune* tune, void* stream);
+
+/* Autotuner: for every (out-degree class, k) bucket of the given queries,
+ * time each candidate configuration (VC / EC, 2 / 4 / 8 / 32 threads per
+ * group, 4 / 32 small roots per claim) on up to `sample` of the bucket's
+ * queries (0 = 256) and keep the fastest in tune_out.  Then time the
+ * assembled table on all the queries against uniform configurations (one
+ * launch for every bucket) and keep whichever is fastest.  Synchronises the
+ * stream. */
+kc_status kc_batch_tune(kc_batch* b, const uint32_t* graph_ids, const uint32_t* ks, uint32_t nq, uint32_t sample,
+                        kc_tune* tune_out, void* stream);
+
+/* Capture the launches of kc_batch_count for these queries into a CUDA
+ * graph (descriptors staged in memory the executable owns).  Every
+ * kc_batch_exec_launch then replays them on `stream`, writing results_dev,
+ * which must stay valid while the executable exists. */
+kc_status kc_batch_capture(kc_batch* b, const uint32_t* graph_ids, const uint32_t* ks, uint32_t nq,
+                           kc_result* results_dev, const kc_tune* tune, kc_batch_exec** out);
+kc_status kc_batch_exec_launch(kc_batch_exec* e, void* stream);
+kc_status kc_batch_exec_destroy(kc_batch_exec* e);
+
 #ifdef __cplusplus
 }
 #endif

@@ -132,6 +132,44 @@ kc_status count_launch(kc_graph* g, const CountArgs& a, kc_result* result_dev, c
 kc_status count_reserve(kc_graph* g, uint32_t k_max, int pivot, int per_vertex, cudaStream_t s);
 size_t ctl_bytes();
 
+// One query of a batched orientation-mode launch: a resident DAG (library
+// numbering), the query's roots in decreasing out-degree, and its k.
+struct QDesc {
+    const uint32_t* rp;
+    const uint32_t* col;
+    const uint32_t* roots;
+    uint32_t n_roots;            // entries of roots (the graph's vertices)
+    uint32_t k;
+    uint32_t n;                  // vertices (the k = 1 answer)
+    uint32_t d_max;              // largest out-degree among the roots
+    unsigned long long m;        // edges (the k = 2 answer)
+    uint32_t slot;               // index of the query's kc_result in the output array
+    uint32_t pad;
+};
+
+// Launch configuration of one group of a batched launch.
+struct BatchConfig {
+    int ec;                      // edge-centric split for the big roots
+    uint32_t subwarp;            // threads per group: 1, 2, 4, 8, 16, 32
+    uint32_t chunk;              // small roots a warp claims per atomic
+};
+
+// Device working memory of one batched launch of nq queries.
+size_t batch_ws_bytes(uint32_t nq);
+
+// Enqueue the counts of q_dev[0, nq) (device array, one configuration) on
+// stream s: working memory ws (batch_ws_bytes(nq) bytes, device, 256-byte
+// aligned), results to results_dev[q.slot].  d_cap / k_max: the
+// largest out-degree and k among the queries.  No allocation, no host
+// synchronisation: safe to capture.
+kc_status batch_launch(const QDesc* q_dev, uint32_t nq, uint32_t d_cap, uint32_t k_max, const BatchConfig& cfg,
+                       void* ws, double time_limit_s, int sm_count, kc_result* results_dev, cudaStream_t s);
+
+// Shared memory a batched launch of this geometry needs, or 0 if it does
+// not fit (bitmaps would need global memory, which batched launches do not
+// take).
+size_t batch_smem_bytes(uint32_t d_cap, uint32_t k_max, const BatchConfig& cfg);
+
 // kc_pivot.cu
 // Fixed-k pivoting count into result_dev (device); per_vertex_dev: n entries
 // (input numbering) or null.

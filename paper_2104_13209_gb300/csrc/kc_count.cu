@@ -50,7 +50,6 @@ struct CountParams {
     uint32_t n_big;            // roots[0, n_big): |C| > 32 and |C| >= k - 1
     uint32_t n_work;           // roots[n_big, n_work): 32 >= |C| >= k - 1
     uint32_t* task_next;       // per big root: next unclaimed task (zeroed before launch)
-    uint32_t claim_div;        // VC: a group claims max(1, d / claim_div) tasks per atomic (0: one task)
     uint32_t help_min;         // join another block's root only if this many tasks are left (0 = never)
     uint32_t dcap, wcap, depth;
     int in_smem;               // bitmaps and stacks in shared memory (else per-block global scratch)
@@ -393,9 +392,10 @@ __device__ bool steal_or_finish(const CountParams& P, StealShared* ss, uint32_t*
 }
 
 // Candidate list of root u into cand[]; returns d.
-__device__ __forceinline__ uint32_t load_root(const CountParams& P, uint32_t u, uint32_t* cand) {
-    const uint32_t b = P.rp[u], d = P.rp[u + 1] - b;
-    for (uint32_t i = threadIdx.x; i < d; i += BLOCK) cand[i] = P.col[b + i];
+__device__ __forceinline__ uint32_t load_root(const uint32_t* __restrict__ rp, const uint32_t* __restrict__ col,
+                                              uint32_t u, uint32_t* cand) {
+    const uint32_t b = rp[u], d = rp[u + 1] - b;
+    for (uint32_t i = threadIdx.x; i < d; i += BLOCK) cand[i] = col[b + i];
     __syncthreads();
     return d;
 }
@@ -421,9 +421,17 @@ __device__ uint32_t next_big_slot(const CountParams& P, WorkCtl* wc, int& phase)
     return NONE;
 }
 
+// One big root u (candidate list N+(u) with more than 32 members) by the
+// whole block: the bitmap of its induced sub-graph, then the level-2 (VC) or
+// root-edge (EC) subtrees claimed by the groups, then stealing until every
+// group is idle.  rp / col: the DAG the root belongs to; k: the clique size
+// of its query; s: the root's slot in P.task_next (used only when other
+// blocks may join, P.help_min != 0).  The caller sets sh.task = 0 and
+// synchronises the block before the call.
 template <int G, bool EC>
-__device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& sh, StealShared& ss, Acc& acc) {
-    WorkCtl* wc = reinterpret_cast<WorkCtl*>(P.ctl + 1);
+__device__ void block_root(const CountParams& P, const uint32_t* __restrict__ rp, const uint32_t* __restrict__ col,
+                           uint32_t k, uint32_t s, uint32_t u, uint32_t* smem, BlockShared& sh, StealShared& ss,
+                           Acc& acc) {
     const uint32_t W0 = P.wcap;
     const uint32_t D0 = (P.dcap + 31) & ~31u;
     uint32_t* cand = smem;
@@ -431,7 +439,7 @@ __device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& s
     uint32_t* bm = region;                                    // dcap x W0
     // edge-centric split: the edge's induced sub-graph is compacted only when
     // the tree below it is deep enough to repay the compaction
-    const bool compact = EC && P.k >= EC_COMPACT_MIN_K;
+    const bool compact = EC && k >= EC_COMPACT_MIN_K;
     uint32_t* sub = bm + (size_t)P.dcap * W0;                      // compaction: dcap x W0
     uint32_t* subidx = sub + (compact ? (size_t)P.dcap * W0 : 0);  // compaction: D0 member positions
     uint32_t* wpre = subidx + (compact ? D0 : 0);                  // compaction: W0 + 1 prefix popcounts
@@ -445,22 +453,13 @@ __device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& s
     const unsigned leader = (threadIdx.x & 31) & ~(unsigned)(G - 1);
     __shared__ uint32_t s_meta[BLOCK][4];  // a taken frame's meta, one row per group leader
     uint32_t* m = s_meta[threadIdx.x / G * G];
-    int phase = 0;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            sh.slot = next_big_slot(P, wc, phase);
-            sh.task = 0;
-        }
-        __syncthreads();
-        const uint32_t s = sh.slot;
-        if (s == NONE) break;
-        const uint32_t u = P.roots[s];
-        const uint32_t d = load_root(P, u, cand);
+    {
+        const uint32_t d = load_root(rp, col, u, cand);
         const uint32_t Wd = (d + 31) >> 5;
         if (P.hash_words)
-            build_bitmap_hashed<BLOCK>(P.rp, P.col, cand, d, Wd, bm, tab, hash_bits_for(d));
+            build_bitmap_hashed<BLOCK>(rp, col, cand, d, Wd, bm, tab, hash_bits_for(d));
         else
-            build_bitmap<BLOCK>(P.rp, P.col, cand, d, Wd, bm);
+            build_bitmap<BLOCK>(rp, col, cand, d, Wd, bm);
         if (!compact) {
             // groups claim level-2 subtrees of this root, then share the deep ones
             if (threadIdx.x == 0) {
@@ -470,8 +469,10 @@ __device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& s
                 for (int x = 0; x < QCAP; ++x) ss.state[x] = 0;
             }
             __syncthreads();
-            const uint32_t rem0 = P.k - 2;
-            const uint32_t claim = P.claim_div ? max(1u, d / P.claim_div) : 1u;
+            const uint32_t rem0 = k - 2;
+            // small trees (k <= 4, vertex-centric): a group claims a few
+            // tasks at a time; otherwise one task (one root edge) per claim
+            const uint32_t claim = (k <= 4 && !EC) ? max(1u, d / (4u * (BLOCK / G))) : 1u;
             for (;;) {
                 uint32_t t0 = 0;
                 // without helpers (help_min = 0) the root's tasks are this
@@ -490,11 +491,12 @@ __device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& s
         } else {
             // one root edge u -> cand[i] at a time: compact C ∩ N+(cand[i]) and
             // let the groups claim its level-3 subtrees
-            const uint32_t rem0 = P.k - 3;
+            const uint32_t rem0 = k - 3;
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
             for (;;) {
                 if (threadIdx.x == 0) {
-                    uint32_t i = timed_out(P.ctl) ? NONE : atomicAdd(&P.task_next[s], 1u);
+                    uint32_t i = timed_out(P.ctl) ? NONE
+                                                  : (P.help_min ? atomicAdd(&P.task_next[s], 1u) : atomicAdd(&sh.task, 1u));
                     sh.edge = (i != NONE && i < d) ? i : NONE;
                     sh.sub_next = 0;
                     ss.idle = 0;
@@ -525,7 +527,7 @@ __device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& s
                 }
                 __syncthreads();
                 const uint32_t de = wpre[Wd];
-                if (de + 2 < P.k) {
+                if (de + 2 < k) {
                     __syncthreads();
                     continue;
                 }
@@ -568,6 +570,24 @@ __device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& s
                 __syncthreads();
             }
         }
+    }
+}
+
+// Big roots of a single-graph launch: own a new root while any is left, then
+// join roots with unclaimed tasks (P.help_min != 0).
+template <int G, bool EC>
+__device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& sh, StealShared& ss, Acc& acc) {
+    WorkCtl* wc = reinterpret_cast<WorkCtl*>(P.ctl + 1);
+    int phase = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            sh.slot = next_big_slot(P, wc, phase);
+            sh.task = 0;
+        }
+        __syncthreads();
+        const uint32_t s = sh.slot;
+        if (s == NONE) break;
+        block_root<G, EC>(P, P.rp, P.col, P.k, s, P.roots[s], smem, sh, ss, acc);
         __syncthreads();
     }
 }
@@ -578,6 +598,8 @@ __device__ void block_phase(const CountParams& P, uint32_t* smem, BlockShared& s
 struct WarpShared {
     uint32_t cand[32];
     uint32_t row[32];
+    uint32_t pre[32];      // exclusive prefix of the rows' popcounts (level-3 task numbering)
+    uint32_t next;         // next unclaimed level-3 task
     uint32_t stk[WARP_DEPTH * 32];
 };
 
@@ -627,10 +649,96 @@ __device__ uint64_t lane_walk(const CountParams& P, uint32_t J0, uint32_t rem0, 
     return acc;
 }
 
+// One small root u (at most 32 candidates) by one warp: one-word rows built
+// cooperatively, then lane i walks the subtree below the root edge
+// u -> cand[i].  rp / col: the root's DAG; k: its query's clique size.
+__device__ void warp_root(const CountParams& P, const uint32_t* __restrict__ rp, const uint32_t* __restrict__ col,
+                          uint32_t k, uint32_t u, WarpShared& ws, Acc& acc) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t rem0 = k - 2;  // below the root edge u -> cand[lane]
+    const uint32_t b = rp[u];
+    const uint32_t d = rp[u + 1] - b;
+    if (lane < (int)d) ws.cand[lane] = col[b + lane];
+    __syncwarp();
+    // rows, one per candidate, built cooperatively (lanes over N+(cand[r]));
+    // lane r holds the bounds of row r, loaded together
+    const uint32_t last = ws.cand[d - 1];
+    uint32_t rb = 0, re = 0;
+    if (lane < (int)d) {
+        rb = __ldg(rp + ws.cand[lane]);
+        re = __ldg(rp + ws.cand[lane] + 1);
+    }
+    for (uint32_t r = 0; r < d; ++r) {
+        const uint32_t xb = __shfl_sync(0xffffffffu, rb, r), xe = __shfl_sync(0xffffffffu, re, r);
+        uint32_t bits = 0;
+        scan_row(col, xb, xe, last, lane, [&](uint32_t y) {
+            const uint32_t pos = find_sorted(ws.cand, r + 1, d, y);
+            if (pos != NONE) bits |= 1u << pos;
+        });
+        bits = __reduce_or_sync(0xffffffffu, bits);
+        if (lane == 0) ws.row[r] = bits;
+    }
+    __syncwarp();
+    if (rem0 <= 2) {
+        // lane i counts below the root edge u -> cand[i] (one or two levels)
+        if (lane < (int)d) {
+            const uint32_t R = ws.row[lane];
+            uint64_t c = 0;
+            if (rem0 == 1) {
+                c = __popc(R);
+            } else {
+                c = edge_count1(R, ws.row);
+                acc.words += __popc(R);
+            }
+            acc.add(c);
+        }
+        __syncwarp();
+        return;
+    }
+    // deeper trees: the level-3 subtrees (u, cand[i], cand[j]), j in row i,
+    // numbered row by row, are claimed one at a time by the lanes, so that a
+    // dense root's work spreads over the warp
+    const uint32_t cnt = lane < (int)d ? __popc(ws.row[lane]) : 0u;
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    ws.pre[lane] = incl - cnt;
+    const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane == 0) ws.next = 0;
+    __syncwarp();
+    const uint32_t rem1 = rem0 - 1;
+    uint64_t c = 0;
+    for (;;) {
+        const uint32_t t = atomicAdd(&ws.next, 1u);
+        if (t >= T) break;
+        uint32_t lo = 0, hi = d;  // the row i with pre[i] <= t < pre[i] + popc(row i)
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (ws.pre[mid] <= t) lo = mid; else hi = mid;
+        }
+        const uint32_t Ri = ws.row[lo];
+        const uint32_t j = __fns(Ri, 0, (int)(t - ws.pre[lo]) + 1);
+        const uint32_t J = Ri & ws.row[j];
+        ++acc.words;
+        if ((uint32_t)__popc(J) < rem1) continue;
+        if (rem1 == 2) {
+            c += edge_count1(J, ws.row);
+            acc.words += __popc(J);
+        } else {
+            c += lane_walk(P, J, rem1, ws.row, ws.stk, acc.words);
+        }
+    }
+    acc.add(c);
+    __syncwarp();
+}
+
+// Small roots of a single-graph launch, one per warp from a global cursor.
 __device__ void warp_phase(const CountParams& P, WarpShared& ws, Acc& acc) {
     WorkCtl* wc = reinterpret_cast<WorkCtl*>(P.ctl + 1);
     const int lane = threadIdx.x & 31;
-    const uint32_t rem0 = P.k - 2;  // below the root edge u -> cand[lane]
     uint32_t iter = 0;
     for (;;) {
         uint32_t i = 0;
@@ -640,44 +748,7 @@ __device__ void warp_phase(const CountParams& P, WarpShared& ws, Acc& acc) {
         }
         i = __shfl_sync(0xffffffffu, i, 0);
         if (i >= P.n_work) break;
-        const uint32_t u = P.roots[i];
-        const uint32_t b = P.rp[u];
-        const uint32_t d = P.rp[u + 1] - b;
-        if (lane < (int)d) ws.cand[lane] = P.col[b + lane];
-        __syncwarp();
-        // rows, one per candidate, built cooperatively (lanes over N+(cand[r]));
-        // lane r holds the bounds of row r, loaded together
-        const uint32_t last = ws.cand[d - 1];
-        uint32_t rb = 0, re = 0;
-        if (lane < (int)d) {
-            rb = __ldg(P.rp + ws.cand[lane]);
-            re = __ldg(P.rp + ws.cand[lane] + 1);
-        }
-        for (uint32_t r = 0; r < d; ++r) {
-            const uint32_t xb = __shfl_sync(0xffffffffu, rb, r), xe = __shfl_sync(0xffffffffu, re, r);
-            uint32_t bits = 0;
-            scan_row(P.col, xb, xe, last, lane, [&](uint32_t y) {
-                const uint32_t pos = find_sorted(ws.cand, r + 1, d, y);
-                if (pos != NONE) bits |= 1u << pos;
-            });
-            bits = __reduce_or_sync(0xffffffffu, bits);
-            if (lane == 0) ws.row[r] = bits;
-        }
-        __syncwarp();
-        // each lane walks the subtree below the root edge u -> cand[lane]
-        if (lane < (int)d) {
-            const uint32_t R = ws.row[lane];
-            uint64_t c = 0;
-            if (rem0 == 1) c = __popc(R);
-            else if (rem0 == 2) {
-                c = edge_count1(R, ws.row);
-                acc.words += __popc(R);
-            } else if ((uint32_t)__popc(R) >= rem0) {
-                c = lane_walk(P, R, rem0, ws.row, ws.stk, acc.words);
-            }
-            acc.add(c);
-        }
-        __syncwarp();
+        warp_root(P, P.rp, P.col, P.k, P.roots[i], ws, acc);
     }
 }
 
@@ -889,8 +960,6 @@ kc_status count_launch(kc_graph* g, const CountArgs& a, kc_result* result_dev, c
     // small trees (k <= 4): a root stays with its block and groups claim a
     // few tasks at a time; deeper trees: one task per claim, and idle blocks
     // join roots that still have unclaimed tasks
-    // edge-centric: every root edge is claimed on its own
-    P.claim_div = (k <= 4 && !ec) ? 4u * (BLOCK / G) : 0u;
     P.help_min = k <= 4 ? 0u : 2u;
     P.dcap = geo.dcap;
     P.wcap = geo.wcap;
@@ -911,6 +980,318 @@ kc_status count_launch(kc_graph* g, const CountArgs& a, kc_result* result_dev, c
         KC_CUDA(cudaGetLastError());
     }
     k_finalize<<<1, 1, 0, s>>>(ctl, result_dev);
+    note_launch();
+    KC_CUDA(cudaGetLastError());
+    return KC_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched counts: many (graph, k) queries in one persistent launch.  The
+// item space is every query's roots with out-degree >= k - 1: first the big
+// roots of all queries (one block each, as block_root), then the small ones
+// (one warp each, as warp_root).  Each query accumulates an exact 128-bit
+// total of its own.
+// ---------------------------------------------------------------------------
+struct BatchCtl {
+    unsigned big_cursor;
+    unsigned small_cursor;
+};
+
+struct BatchParams {
+    CountParams base;           // geometry and control record (graph fields unused)
+    const QDesc* q;
+    uint32_t nq;
+    uint32_t chunk;             // small roots per claim
+    const uint32_t* nbig;       // per query: roots with more than 32 candidates
+    const uint32_t* big_pre;    // exclusive prefix sums, nq + 1 entries
+    const uint32_t* small_pre;
+    unsigned long long* out;    // per query: total low, total high, words
+    BatchCtl* bc;
+};
+
+// the query whose item range [pre[q], pre[q + 1]) holds item i (i < pre[nq])
+__device__ __forceinline__ uint32_t find_query(const uint32_t* pre, uint32_t nq, uint32_t i) {
+    uint32_t lo = 0, hi = nq;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (pre[mid + 1] <= i) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// exact warp sum of the lanes' partials into out3 (all 32 lanes call it)
+__device__ __forceinline__ void flush_warp_acc(Acc& acc, unsigned long long* out3) {
+    unsigned long long lo = acc.lo, hi = acc.hi, words = acc.words;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, lo, o);
+        const unsigned long long yh = __shfl_xor_sync(0xffffffffu, hi, o);
+        words += __shfl_xor_sync(0xffffffffu, words, o);
+        const unsigned long long sum = lo + y;
+        hi += yh + (sum < lo ? 1ull : 0ull);
+        lo = sum;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        add_u128(&out3[0], &out3[1], lo);
+        if (hi) atomicAdd(&out3[1], hi);
+        if (words) atomicAdd(&out3[2], words);
+    }
+    acc = Acc();
+}
+
+// roots (decreasing out-degree) with out-degree >= t
+__device__ __forceinline__ uint32_t roots_at_least(const uint32_t* rp, const uint32_t* roots, uint32_t n, uint32_t t) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const uint32_t r = roots[mid];
+        if (rp[r + 1] - rp[r] >= t) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_batch_prep(const QDesc* __restrict__ q, uint32_t nq, uint32_t* __restrict__ nbig,
+                             uint32_t* __restrict__ nwork) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    const QDesc D = q[i];
+    if (D.k < 3 || D.k > D.d_max + 1) {
+        nbig[i] = nwork[i] = 0;
+        return;
+    }
+    nwork[i] = roots_at_least(D.rp, D.roots, D.n_roots, D.k - 1);
+    nbig[i] = roots_at_least(D.rp, D.roots, D.n_roots, max(D.k - 1, (uint32_t)SMALL_D + 1));
+}
+
+// exclusive prefix sums of nbig and of nwork - nbig (one block of 1024)
+__global__ void __launch_bounds__(1024) k_batch_scan(const uint32_t* __restrict__ nbig,
+                                                      const uint32_t* __restrict__ nwork, uint32_t nq,
+                                                      uint32_t* __restrict__ big_pre, uint32_t* __restrict__ small_pre) {
+    __shared__ uint32_t wb[32], wsm[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t cb = 0, cs = 0;
+    for (uint32_t base = 0; base < nq; base += 1024) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t b = i < nq ? nbig[i] : 0, sm = i < nq ? nwork[i] - nbig[i] : 0;
+        uint32_t ib = b, is = sm;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t yb = __shfl_up_sync(0xffffffffu, ib, o), ys = __shfl_up_sync(0xffffffffu, is, o);
+            if (lane >= o) {
+                ib += yb;
+                is += ys;
+            }
+        }
+        if (lane == 31) {
+            wb[warp] = ib;
+            wsm[warp] = is;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t xb = wb[lane], xs = wsm[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t yb = __shfl_up_sync(0xffffffffu, xb, o), ys = __shfl_up_sync(0xffffffffu, xs, o);
+                if (lane >= o) {
+                    xb += yb;
+                    xs += ys;
+                }
+            }
+            wb[lane] = xb;
+            wsm[lane] = xs;
+        }
+        __syncthreads();
+        const uint32_t ob = cb + (warp ? wb[warp - 1] : 0u) + ib - b;
+        const uint32_t os = cs + (warp ? wsm[warp - 1] : 0u) + is - sm;
+        if (i < nq) {
+            big_pre[i] = ob;
+            small_pre[i] = os;
+        }
+        cb += wb[31];
+        cs += wsm[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        big_pre[nq] = cb;
+        small_pre[nq] = cs;
+    }
+}
+
+template <int G, bool EC>
+__global__ void __launch_bounds__(BLOCK) k_count_batch(const BatchParams B) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ BlockShared sh;
+    __shared__ StealShared ss;
+    __shared__ uint32_t s_q, s_u;
+    const uint32_t nbig_total = B.big_pre[B.nq];
+    const uint32_t nsmall_total = B.small_pre[B.nq];
+    Acc acc;
+    while (nbig_total) {
+        if (threadIdx.x == 0) {
+            const uint32_t i = timed_out(B.base.ctl) ? NONE : atomicAdd(&B.bc->big_cursor, 1u);
+            uint32_t q = NONE, u = 0;
+            if (i < nbig_total) {
+                q = find_query(B.big_pre, B.nq, i);
+                u = B.q[q].roots[i - B.big_pre[q]];
+            }
+            s_q = q;
+            s_u = u;
+            sh.task = 0;
+        }
+        __syncthreads();
+        const uint32_t q = s_q;
+        if (q == NONE) break;
+        const QDesc* D = B.q + q;
+        block_root<G, EC>(B.base, D->rp, D->col, D->k, 0, s_u, smem, sh, ss, acc);
+        flush_warp_acc(acc, B.out + 3 * (size_t)q);
+        __syncthreads();
+    }
+    __syncthreads();
+    if (nsmall_total == 0) return;
+    WarpShared* ws = reinterpret_cast<WarpShared*>(smem) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    uint32_t cur = NONE, lo = 0, hi = 0;  // the current query and its item range
+    for (;;) {
+        uint32_t j = 0;
+        if (lane == 0) j = timed_out(B.base.ctl) ? NONE : atomicAdd(&B.bc->small_cursor, B.chunk);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        if (j >= nsmall_total) break;
+        const uint32_t j1 = min(j + B.chunk, nsmall_total);
+        for (uint32_t t = j; t < j1; ++t) {
+            if (t < lo || t >= hi) {
+                const uint32_t q = find_query(B.small_pre, B.nq, t);
+                if (cur != NONE) flush_warp_acc(acc, B.out + 3 * (size_t)cur);
+                cur = q;
+                lo = B.small_pre[q];
+                hi = B.small_pre[q + 1];
+            }
+            const QDesc* D = B.q + cur;
+            warp_root(B.base, D->rp, D->col, D->k, D->roots[B.nbig[cur] + (t - lo)], *ws, acc);
+        }
+    }
+    if (cur != NONE) flush_warp_acc(acc, B.out + 3 * (size_t)cur);
+}
+
+__global__ void k_batch_finalize(const QDesc* __restrict__ q, uint32_t nq, const unsigned long long* __restrict__ out,
+                                 const Ctl* ctl, kc_result* __restrict__ res) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    const QDesc D = q[i];
+    kc_result r;
+    r.total = 0;
+    r.total_hi = 0;
+    r.flags = 0;
+    r.status = KC_OK;
+    r.words = 0;
+    if (D.k == 1) {
+        r.total = D.n;
+    } else if (D.k == 2) {
+        r.total = D.m;
+    } else if (D.k <= D.d_max + 1) {
+        r.total = out[3 * (size_t)i];
+        r.total_hi = out[3 * (size_t)i + 1];
+        r.words = out[3 * (size_t)i + 2];
+        if (r.total_hi) r.flags |= KC_FLAG_TOTAL_OVERFLOW;
+    }
+    if (ctl->flags & KC_FLAG_TIMEOUT) {
+        r.flags |= KC_FLAG_TIMEOUT;
+        r.status = KC_E_TIMEOUT;
+    }
+    res[D.slot] = r;
+}
+
+typedef void (*BatchKernel)(const BatchParams);
+
+template <bool EC>
+static BatchKernel pick_batch(uint32_t G) {
+    switch (G) {
+        case 1: return k_count_batch<1, EC>;
+        case 2: return k_count_batch<2, EC>;
+        case 4: return k_count_batch<4, EC>;
+        case 8: return k_count_batch<8, EC>;
+        case 16: return k_count_batch<16, EC>;
+        default: return k_count_batch<32, EC>;
+    }
+}
+
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t batch_ws_bytes(uint32_t nq) {
+    return al256(sizeof(Ctl) + sizeof(BatchCtl)) + 4 * al256(((size_t)nq + 1) * 4) + al256((size_t)nq * 24 + 8);
+}
+
+size_t batch_smem_bytes(uint32_t d_cap, uint32_t k_max, const BatchConfig& cfg) {
+    const Geometry geo = plan_geometry(std::max<uint32_t>(d_cap, 1), std::max<uint32_t>(k_max, 3), cfg.subwarp,
+                                       cfg.ec != 0);
+    return geo.in_smem ? geo.smem_bytes : 0;
+}
+
+kc_status batch_launch(const QDesc* q_dev, uint32_t nq, uint32_t d_cap, uint32_t k_max, const BatchConfig& cfg,
+                       void* ws, double time_limit_s, int sm_count, kc_result* results_dev, cudaStream_t s) {
+    if (nq == 0) return KC_OK;
+    const uint32_t G = cfg.subwarp;
+    if (G != 1 && G != 2 && G != 4 && G != 8 && G != 16 && G != 32)
+        return set_error(KC_E_INVALID_ARG, "subwarp must be 1, 2, 4, 8, 16 or 32");
+    if (k_max > MAX_DEPTH + 4)
+        return set_error(KC_E_UNSUPPORTED, "orientation traversal supports k <= %d", MAX_DEPTH + 4);
+    char* p = (char*)ws;
+    Ctl* ctl = (Ctl*)p;
+    BatchCtl* bc = (BatchCtl*)(ctl + 1);
+    p += al256(sizeof(Ctl) + sizeof(BatchCtl));
+    uint32_t* nbig = (uint32_t*)p;
+    p += al256(((size_t)nq + 1) * 4);
+    uint32_t* nwork = (uint32_t*)p;
+    p += al256(((size_t)nq + 1) * 4);
+    uint32_t* big_pre = (uint32_t*)p;
+    p += al256(((size_t)nq + 1) * 4);
+    uint32_t* small_pre = (uint32_t*)p;
+    p += al256(((size_t)nq + 1) * 4);
+    unsigned long long* out = (unsigned long long*)p;
+    KC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl) + sizeof(BatchCtl), s));
+    KC_CUDA(cudaMemsetAsync(out, 0, (size_t)nq * 24, s));
+    const unsigned qb = (nq + 255) / 256;
+    k_batch_prep<<<qb, 256, 0, s>>>(q_dev, nq, nbig, nwork);
+    note_launch();
+    k_batch_scan<<<1, 1024, 0, s>>>(nbig, nwork, nq, big_pre, small_pre);
+    note_launch();
+    const unsigned long long budget = time_limit_s > 0 ? (unsigned long long)(time_limit_s * 1e9) : 0ull;
+    k_set_deadline<<<1, 1, 0, s>>>(ctl, budget);
+    note_launch();
+    KC_CUDA(cudaGetLastError());
+    if (k_max >= 3 && d_cap >= 2) {
+        const Geometry geo = plan_geometry(d_cap, k_max, G, cfg.ec != 0);
+        if (!geo.in_smem)
+            return set_error(KC_E_UNSUPPORTED, "batched launches need out-degrees whose bitmaps fit in shared "
+                                               "memory (largest out-degree %u)", d_cap);
+        BatchKernel kern = cfg.ec ? pick_batch<true>(G) : pick_batch<false>(G);
+        KC_CUDA(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)geo.smem_bytes));
+        int bps = 0;
+        KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, BLOCK, geo.smem_bytes));
+        if (bps < 1) return set_error(KC_E_UNSUPPORTED, "batch kernel cannot be resident (smem %zu)", geo.smem_bytes);
+        BatchParams B;
+        memset(&B, 0, sizeof(B));
+        B.base.dcap = geo.dcap;
+        B.base.wcap = geo.wcap;
+        B.base.depth = geo.depth;
+        B.base.in_smem = 1;
+        B.base.hash_words = geo.hash_words;
+        B.base.help_min = 0;
+        B.base.ctl = ctl;
+        B.q = q_dev;
+        B.nq = nq;
+        B.chunk = std::max<uint32_t>(cfg.chunk, 1);
+        B.nbig = nbig;
+        B.big_pre = big_pre;
+        B.small_pre = small_pre;
+        B.out = out;
+        B.bc = bc;
+        kern<<<bps * sm_count, BLOCK, geo.smem_bytes, s>>>(B);
+        note_launch();
+        KC_CUDA(cudaGetLastError());
+    }
+    k_batch_finalize<<<qb, 256, 0, s>>>(q_dev, nq, out, ctl, results_dev);
     note_launch();
     KC_CUDA(cudaGetLastError());
     return KC_OK;
@@ -1000,7 +1381,6 @@ extern "C" kc_status kc_count_noalloc(const kc_graph* g, uint32_t k, int scheme,
     P.n_big = (uint32_t)n_big;
     P.n_work = (uint32_t)n_work;
     P.task_next = task_next;
-    P.claim_div = (k <= 4 && !ec) ? 4u * (BLOCK / G) : 0u;
     P.help_min = k <= 4 ? 0u : 2u;
     P.dcap = geo.dcap;
     P.wcap = geo.wcap;

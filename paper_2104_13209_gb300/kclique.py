@@ -46,6 +46,8 @@ EXPORTED = [
     "kc_last_error", "kc_status_name", "kc_version", "kc_graph_create", "kc_graph_destroy", "kc_graph_info_get",
     "kc_graph_export", "kc_count", "kc_count128", "kc_count_async", "kc_count_noalloc", "kc_graph_reserve", "kc_count_all",
     "kc_graph_set_time_limit", "kc_launch_count", "kc_graph_last_work",
+    "kc_batch_create", "kc_batch_destroy", "kc_batch_graph_info", "kc_batch_set_time_limit", "kc_batch_count",
+    "kc_batch_tune", "kc_batch_capture", "kc_batch_exec_launch", "kc_batch_exec_destroy",
 ]
 
 
@@ -58,6 +60,18 @@ class kc_graph_info(ctypes.Structure):
 class kc_result(ctypes.Structure):
     _fields_ = [("total", ctypes.c_uint64), ("total_hi", ctypes.c_uint64), ("flags", ctypes.c_uint32),
                 ("status", ctypes.c_uint32), ("words", ctypes.c_uint64)]
+
+
+KC_TUNE_MAX = 256
+
+
+class kc_tune_entry(ctypes.Structure):
+    _fields_ = [("dclass", ctypes.c_uint32), ("k", ctypes.c_uint32), ("scheme", ctypes.c_int32),
+                ("subwarp", ctypes.c_uint32), ("chunk", ctypes.c_uint32), ("ms", ctypes.c_float)]
+
+
+class kc_tune(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("e", kc_tune_entry * KC_TUNE_MAX)]
 
 
 RESULT_BYTES = ctypes.sizeof(kc_result)
@@ -110,6 +124,18 @@ def load(build_if_missing: bool = False):
     lib.kc_graph_set_time_limit.argtypes = [vp, ctypes.c_double]
     lib.kc_graph_last_work.argtypes = [vp, ctypes.POINTER(u64)]
     lib.kc_graph_last_work.restype = i32
+    lib.kc_batch_create.argtypes = [vp, vp, u32, u64, vp, u32, i32, i32, i32, vp, ctypes.POINTER(vp)]
+    lib.kc_batch_destroy.argtypes = [vp]
+    lib.kc_batch_graph_info.argtypes = [vp, u32, ctypes.POINTER(u32), ctypes.POINTER(u64), ctypes.POINTER(u32)]
+    lib.kc_batch_set_time_limit.argtypes = [vp, ctypes.c_double]
+    lib.kc_batch_count.argtypes = [vp, vp, vp, u32, vp, vp, vp]
+    lib.kc_batch_tune.argtypes = [vp, vp, vp, u32, u32, ctypes.POINTER(kc_tune), vp]
+    lib.kc_batch_capture.argtypes = [vp, vp, vp, u32, vp, vp, ctypes.POINTER(vp)]
+    lib.kc_batch_exec_launch.argtypes = [vp, vp]
+    lib.kc_batch_exec_destroy.argtypes = [vp]
+    for f in ("kc_batch_create", "kc_batch_destroy", "kc_batch_graph_info", "kc_batch_set_time_limit",
+              "kc_batch_count", "kc_batch_tune", "kc_batch_capture", "kc_batch_exec_launch", "kc_batch_exec_destroy"):
+        getattr(lib, f).restype = i32
     for f in ("kc_graph_create", "kc_graph_destroy", "kc_graph_info_get", "kc_graph_export", "kc_count",
               "kc_count128", "kc_count_async", "kc_count_noalloc", "kc_graph_reserve", "kc_count_all", "kc_graph_set_time_limit"):
         getattr(lib, f).restype = i32
@@ -169,6 +195,7 @@ class CountResult:
     flags: int
     overflow: bool        # exceeded 2^64 - 1
     words: int = 0        # bitmap words intersected by the traversal
+    status: int = KC_OK   # per-query status of a batched count
 
     @property
     def total_u64(self) -> int:
@@ -282,6 +309,142 @@ class Graph:
 
     def reserve(self, k_max: int, pivot: bool = False, per_vertex: bool = False, stream=None):
         _check(load().kc_graph_reserve(self._h, k_max, int(pivot), int(per_vertex), _stream_ptr(stream)))
+
+
+class Batch:
+    """Many small graphs oriented as one block-diagonal union
+    (kc_batch_create); queries (graph, k) counted in persistent launches."""
+
+    def __init__(self, graphs=None, row_ptr=None, col_idx=None, offsets=None, orient: str = "degeneracy",
+                 validate: bool = True, stream=None):
+        from . import synth
+
+        lib = load()
+        if graphs is not None:
+            u, offsets = synth.block_union(graphs)
+            row_ptr, col_idx = u.row_ptr, u.col_idx
+        rp, rp_keep, rp_dev = _ptr_of(row_ptr if _is_torch(row_ptr) else np.asarray(row_ptr, dtype=np.uint32))
+        ci, ci_keep, ci_dev = _ptr_of(col_idx if _is_torch(col_idx) else np.asarray(col_idx, dtype=np.uint32))
+        if rp_dev != ci_dev:
+            raise ValueError("row_ptr and col_idx must both be on the host or both on the device")
+        off = np.ascontiguousarray(offsets, dtype=np.uint32)
+        n = int(off[-1])
+        nnz = ci_keep.numel() if _is_torch(ci_keep) else ci_keep.size
+        h = ctypes.c_void_p()
+        _check(lib.kc_batch_create(rp, ci if nnz else None, n, nnz, off.ctypes.data, off.size - 1, int(rp_dev),
+                                   _ORIENT[orient], int(validate), _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+        self.num_graphs = off.size - 1
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().kc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def graph_info(self, g: int):
+        n, m, d = ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_uint32()
+        _check(load().kc_batch_graph_info(self._h, g, ctypes.byref(n), ctypes.byref(m), ctypes.byref(d)))
+        return {"n": n.value, "m": m.value, "d_max": d.value}
+
+    def set_time_limit(self, seconds: float):
+        _check(load().kc_batch_set_time_limit(self._h, float(seconds)))
+
+    @staticmethod
+    def _queries(graph_ids, ks):
+        gid = np.ascontiguousarray(graph_ids, dtype=np.uint32)
+        kk = np.ascontiguousarray(ks, dtype=np.uint32)
+        if gid.shape != kk.shape:
+            raise ValueError("graph_ids and ks differ in length")
+        return gid, kk
+
+    def count_async(self, graph_ids, ks, results_dev, tune=None, stream=None):
+        """Enqueue the queries; results_dev: CUDA uint8 tensor of len * RESULT_BYTES."""
+        gid, kk = self._queries(graph_ids, ks)
+        p, _, dev = _ptr_of(results_dev)
+        if not dev:
+            raise ValueError("results_dev must be device memory")
+        _check(load().kc_batch_count(self._h, gid.ctypes.data, kk.ctypes.data, gid.size, p,
+                                     ctypes.byref(tune) if tune is not None else None, _stream_ptr(stream)))
+
+    def count(self, graph_ids, ks, tune=None, stream=None) -> list[CountResult]:
+        """Synchronous counts of the queries, in query order."""
+        import torch
+
+        gid, kk = self._queries(graph_ids, ks)
+        res = torch.zeros(max(1, gid.size) * RESULT_BYTES, dtype=torch.uint8, device="cuda")
+        self.count_async(gid, kk, res, tune=tune, stream=stream)
+        if stream is not None:
+            stream.synchronize()
+        torch.cuda.synchronize()
+        return parse_results(bytes(res.cpu().numpy()), gid.size)
+
+    def tune(self, graph_ids, ks, sample: int = 0, stream=None) -> kc_tune:
+        gid, kk = self._queries(graph_ids, ks)
+        t = kc_tune()
+        _check(load().kc_batch_tune(self._h, gid.ctypes.data, kk.ctypes.data, gid.size, sample, ctypes.byref(t),
+                                    _stream_ptr(stream)))
+        return t
+
+    def capture(self, graph_ids, ks, results_dev, tune=None) -> "BatchExec":
+        gid, kk = self._queries(graph_ids, ks)
+        p, keep, dev = _ptr_of(results_dev)
+        if not dev:
+            raise ValueError("results_dev must be device memory")
+        h = ctypes.c_void_p()
+        _check(load().kc_batch_capture(self._h, gid.ctypes.data, kk.ctypes.data, gid.size, p,
+                                       ctypes.byref(tune) if tune is not None else None, ctypes.byref(h)))
+        return BatchExec(h, keep)
+
+
+class BatchExec:
+    """A captured CUDA graph of one batch of queries (kc_batch_capture)."""
+
+    def __init__(self, h, keep):
+        self._h = h
+        self._keep = keep
+
+    def launch(self, stream=None):
+        _check(load().kc_batch_exec_launch(self._h, _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().kc_batch_exec_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tune_to_list(t: kc_tune) -> list[dict]:
+    return [{"dclass": t.e[i].dclass, "k": t.e[i].k, "scheme": t.e[i].scheme, "subwarp": t.e[i].subwarp,
+             "chunk": t.e[i].chunk, "ms": t.e[i].ms} for i in range(t.n)]
+
+
+def tune_from_list(entries: list[dict]) -> kc_tune:
+    t = kc_tune()
+    for i, e in enumerate(entries[:KC_TUNE_MAX]):
+        t.e[i] = kc_tune_entry(e["dclass"], e["k"], e["scheme"], e["subwarp"], e["chunk"], e.get("ms", 0.0))
+    t.n = min(len(entries), KC_TUNE_MAX)
+    return t
+
+
+def parse_results(raw: bytes, n: int) -> list[CountResult]:
+    """n consecutive kc_result records (a device result array read back)."""
+    out = []
+    for i in range(n):
+        r = kc_result.from_buffer_copy(raw[i * RESULT_BYTES:(i + 1) * RESULT_BYTES])
+        total = (r.total_hi << 64) | r.total
+        out.append(CountResult(total, r.flags, total >= (1 << 64), r.words, r.status))
+    return out
 
 
 def parse_result(raw: bytes) -> CountResult:

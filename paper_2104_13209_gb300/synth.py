@@ -336,3 +336,100 @@ def chung_lu_planted(n: int, beta: float = 2.1, mean_deg: float = 30.0, ncomm: i
             start += s
             pair_base += a.size
     return edges_to_csr(n, np.concatenate(us), np.concatenate(vs), f"CL{n}-b{beta}-d{mean_deg}-c{ncomm}s{seed}")
+
+
+# ----------------------------------------------------------------------------
+# Barabasi-Albert graphs and their ego networks (many small graphs)
+# ----------------------------------------------------------------------------
+
+def barabasi_albert(n: int, m: int, seed: int = 0) -> CSRGraph:
+    """Preferential attachment (Barabasi and Albert, 1999) from a seed clique
+    of m + 1 vertices: vertex t >= m + 1 draws m endpoints, each a uniformly
+    chosen entry of the endpoint list of every earlier edge (so an earlier
+    vertex is chosen with probability proportional to its degree).  Draw j of
+    vertex t is counter (t - m - 1) * m + j of stream (seed, 0xBA).  Repeated
+    picks of one vertex collapse into one edge, so a few vertices get fewer
+    than m edges.  The endpoint list is never materialised: position p of it
+    is resolved by following earlier draws (an odd position of a new edge is
+    that edge's own draw), all draws at once.
+    """
+    m0 = m + 1
+    if n < m0:
+        raise ValueError("n must be at least m + 1")
+    su, sv = np.triu_indices(m0, 1)
+    seed_end = np.empty(2 * su.size, dtype=np.int64)
+    seed_end[0::2] = su
+    seed_end[1::2] = sv
+    e_seed = su.size
+    nt = n - m0
+    cnt = np.arange(nt * m, dtype=np.uint64)
+    edge = np.arange(nt * m, dtype=np.int64)
+    src = m0 + edge // m
+    # draws of edge e: a position among the 2 * (edges before its vertex)
+    before = e_seed + (edge // m) * m
+    pos = np.floor(uniform(stream_key(seed, 0xBA), cnt) * (2 * before)).astype(np.int64)
+    pos = np.minimum(pos, 2 * before - 1)
+    tgt = np.full(nt * m, -1, dtype=np.int64)
+    cur = pos.copy()
+    todo = np.arange(nt * m)
+    for _ in range(200):
+        if todo.size == 0:
+            break
+        p = cur[todo]
+        in_seed = p < 2 * e_seed
+        tgt[todo[in_seed]] = seed_end[p[in_seed]]
+        q = p[~in_seed] - 2 * e_seed
+        rest = todo[~in_seed]
+        even = (q % 2) == 0
+        tgt[rest[even]] = m0 + (q[even] // 2) // m       # the source of an earlier new edge
+        cur[rest[~even]] = pos[q[~even] // 2]             # the target of an earlier new edge: its draw
+        todo = rest[~even]
+    if todo.size:
+        raise RuntimeError("endpoint resolution did not converge")
+    u = np.concatenate([su, src])
+    v = np.concatenate([sv, tgt])
+    return edges_to_csr(n, u, v, f"BA{n}-m{m}s{seed}")
+
+
+def ego_network(g: CSRGraph, c: int) -> CSRGraph:
+    """Radius-1 ego network of c: c, its neighbours and every edge among
+    them, relabelled 0..size-1 in increasing id order."""
+    rp, ci = g.row_ptr, g.col_idx
+    nodes = np.unique(np.concatenate([[c], ci[rp[c]:rp[c + 1]]]).astype(np.int64))
+    us, vs = [], []
+    for i, x in enumerate(nodes.tolist()):
+        nb = ci[rp[x]:rp[x + 1]].astype(np.int64)
+        j = np.searchsorted(nodes, nb)
+        j = np.minimum(j, nodes.size - 1)
+        hit = nodes[j] == nb
+        us.append(np.full(int(hit.sum()), i, dtype=np.int64))
+        vs.append(j[hit])
+    return edges_to_csr(int(nodes.size), np.concatenate(us), np.concatenate(vs), f"ego{c}")
+
+
+def ego_networks(g: CSRGraph, count: int, size_min: int, size_max: int, seed: int = 0) -> list[CSRGraph]:
+    """`count` ego networks of distinct centres drawn uniformly (a seeded
+    permutation, stream (seed, 0xE6)) among the vertices whose ego network
+    has size_min..size_max vertices (degree + 1)."""
+    deg = np.diff(g.row_ptr.astype(np.int64))
+    ok = np.nonzero((deg + 1 >= size_min) & (deg + 1 <= size_max))[0]
+    if ok.size < count:
+        raise ValueError(f"only {ok.size} eligible centres")
+    centres = ok[random_permutation(ok.size, seed, 0xE6)[:count]]
+    return [ego_network(g, int(c)) for c in centres]
+
+
+def block_union(graphs: list[CSRGraph]) -> tuple[CSRGraph, np.ndarray]:
+    """Block-diagonal union of the graphs and the vertex offsets (len + 1)."""
+    off = np.zeros(len(graphs) + 1, dtype=np.uint32)
+    np.cumsum([h.n for h in graphs], out=off[1:])
+    rps, cis, base_e = [np.zeros(1, dtype=np.uint64)], [], 0
+    for h, o in zip(graphs, off[:-1]):
+        rps.append(h.row_ptr[1:].astype(np.uint64) + np.uint64(base_e))
+        cis.append(h.col_idx.astype(np.uint64) + np.uint64(o))
+        base_e += int(h.row_ptr[-1])
+    if base_e >= (1 << 32):
+        raise ValueError("nnz does not fit in u32")
+    rp = np.concatenate(rps).astype(np.uint32)
+    ci = (np.concatenate(cis) if cis else np.zeros(0, dtype=np.uint64)).astype(np.uint32)
+    return CSRGraph(int(off[-1]), rp, ci, f"union{len(graphs)}"), off

@@ -287,6 +287,65 @@ kc_status kc_batch_capture(kc_batch* b, const uint32_t* graph_ids, const uint32_
 kc_status kc_batch_exec_launch(kc_batch_exec* e, void* stream);
 kc_status kc_batch_exec_destroy(kc_batch_exec* e);
 
+/* ---- serving ----------------------------------------------------------------
+ * No counterpart in the paper.  A server keeps oriented graphs resident and
+ * answers count queries (graph, k, pivot) from a worker thread of its own:
+ * orientation-mode queries that arrive while others run are packed, up to
+ * max_batch at a time, into persistent batched launches on `slots` streams
+ * that overlap on the device, and each query's result is served as soon as
+ * its last root completes.  Pivot-mode queries (Fig. 3, fixed k), and
+ * orientation queries whose bitmaps exceed shared memory, run one at a time
+ * on the graph's own path.  Counts are those of kc_count / kc_count128. */
+typedef struct kc_server kc_server;
+
+typedef struct kc_server_result {
+    uint64_t total;        /* count modulo 2^64 */
+    uint64_t total_hi;     /* high word (orientation mode; exact below 2^128) */
+    uint32_t flags;        /* KC_FLAG_* */
+    int32_t status;        /* KC_OK, KC_E_TIMEOUT, ... */
+    uint32_t graph_id;
+    uint32_t k;
+    int32_t pivot;
+    uint32_t launch;       /* the launch that served it (1, 2, ...) */
+    double t_submit_ms;    /* times since the server's creation (host clock) */
+    double t_admit_ms;
+    double t_done_ms;
+} kc_server_result;
+
+/* One launch in flight at a time, one query per launch (the plain baseline). */
+#define KC_SERVER_SERIAL 1
+
+/* hbm_budget: device bytes the server may keep resident (slots and graphs);
+ * a graph that would exceed it is refused with KC_E_NO_MEMORY.
+ * max_batch >= 1 queries per batched launch; slots >= 1 batched launches in
+ * flight.  flags: 0 or KC_SERVER_SERIAL.  The calling thread's current
+ * device is the server's. */
+kc_status kc_server_create(size_t hbm_budget, uint32_t max_batch, uint32_t slots, int flags, kc_server** out);
+
+/* Add a graph (arguments as kc_graph_create; the server orients and keeps
+ * it); *graph_id receives its id (0, 1, ...). */
+kc_status kc_server_add_graph(kc_server* s, const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n,
+                              uint64_t nnz, int ptrs_on_device, int orient, int validate, uint32_t* graph_id);
+
+/* Time limit of each launch in seconds (0 = none): a query not finished by
+ * then is answered with KC_E_TIMEOUT; the others of its launch are not
+ * affected. */
+kc_status kc_server_set_time_limit(kc_server* s, double seconds);
+
+/* Queue a query; *ticket identifies it.  Thread-safe. */
+kc_status kc_server_submit(kc_server* s, uint32_t graph_id, uint32_t k, int pivot, uint64_t* ticket);
+
+/* Wait up to timeout_ms (< 0: no limit) for a query; KC_OK with *out
+ * filled when it is done (its own status is out->status), KC_E_TIMEOUT if
+ * it is not done yet.  Thread-safe. */
+kc_status kc_server_poll(kc_server* s, uint64_t ticket, kc_server_result* out, int timeout_ms);
+
+/* Launches so far, queries served, resident device bytes (nullable). */
+kc_status kc_server_stats(kc_server* s, uint64_t* launches, uint64_t* served, uint64_t* resident_bytes);
+
+/* Stop the worker after the launches in flight and free everything. */
+kc_status kc_server_destroy(kc_server* s);
+
 #ifdef __cplusplus
 }
 #endif

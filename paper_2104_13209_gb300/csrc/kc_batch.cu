@@ -160,6 +160,7 @@ static kc_status make_plan(const kc_batch* b, const uint32_t* graph_ids, const u
                            const kc_tune* tune, const BatchConfig* force, Plan& P) {
     struct Item {
         std::tuple<int, uint32_t, uint32_t> key;
+        double cost;
         uint32_t idx;
     };
     std::vector<Item> items(nq);
@@ -170,9 +171,13 @@ static kc_status make_plan(const kc_batch* b, const uint32_t* graph_ids, const u
         if (k > 68) return set_error(KC_E_UNSUPPORTED, "query %u: orientation traversal supports k <= 68", i);
         const BatchConfig c = force ? *force : config_for(tune, dclass_of(b->dmax[g]), k);
         items[i].key = std::make_tuple(c.ec, c.subwarp, c.chunk);
+        items[i].cost = query_cost_estimate(b->m[g], b->dmax[g], k);
         items[i].idx = i;
     }
-    std::stable_sort(items.begin(), items.end(), [](const Item& x, const Item& y) { return x.key < y.key; });
+    // launches by configuration; inside one, cheapest queries first
+    std::stable_sort(items.begin(), items.end(), [](const Item& x, const Item& y) {
+        return x.key != y.key ? x.key < y.key : x.cost < y.cost;
+    });
     P.q.resize(nq);
     P.groups.clear();
     size_t off_ws = al((size_t)nq * sizeof(QDesc) + 16);
@@ -226,7 +231,7 @@ static kc_status enqueue_plan(const kc_batch* b, const Plan& P, void* stage, cha
     const QDesc* qd = (const QDesc*)ws;
     for (const Group& G : P.groups)
         KC_CHECK(batch_launch(qd + G.first, G.count, G.d_cap, G.k_max, G.cfg, ws + G.ws_off, b->g->time_limit_s,
-                              b->g->sm_count, results_dev, s));
+                              b->g->sm_count, results_dev, nullptr, nullptr, s));
     return KC_OK;
 }
 

@@ -154,6 +154,15 @@ struct BatchConfig {
     uint32_t chunk;              // small roots a warp claims per atomic
 };
 
+// Rough cost of a query, used only to order the queries of a launch
+// cheapest first: m * d_max^(min(k, 6) - 2) for 3 <= k <= d_max + 1.
+inline double query_cost_estimate(unsigned long long m, uint32_t d_max, uint32_t k) {
+    if (k < 3 || k > d_max + 1) return 0.0;
+    double c = (double)m;
+    for (uint32_t i = 2; i < (k < 6 ? k : 6); ++i) c *= (double)d_max;
+    return c;
+}
+
 // Device working memory of one batched launch of nq queries.
 size_t batch_ws_bytes(uint32_t nq);
 
@@ -162,8 +171,14 @@ size_t batch_ws_bytes(uint32_t nq);
 // aligned), results to results_dev[q.slot].  d_cap / k_max: the
 // largest out-degree and k among the queries.  No allocation, no host
 // synchronisation: safe to capture.
+// early / done (nullable together): each query's result is also written to
+// early[slot], then done[slot] = 1 after a system-scope fence, as soon as its
+// last root completes (before the launch ends); host-mapped memory lets a
+// host thread see results while the launch still runs.  A query that timed
+// out is not published early; its results_dev entry has KC_E_TIMEOUT.
 kc_status batch_launch(const QDesc* q_dev, uint32_t nq, uint32_t d_cap, uint32_t k_max, const BatchConfig& cfg,
-                       void* ws, double time_limit_s, int sm_count, kc_result* results_dev, cudaStream_t s);
+                       void* ws, double time_limit_s, int sm_count, kc_result* results_dev, kc_result* early,
+                       unsigned* done, cudaStream_t s);
 
 // Shared memory a batched launch of this geometry needs, or 0 if it does
 // not fit (bitmaps would need global memory, which batched launches do not

@@ -1008,7 +1008,52 @@ struct BatchParams {
     const uint32_t* small_pre;
     unsigned long long* out;    // per query: total low, total high, words
     BatchCtl* bc;
+    unsigned* remaining;        // per query: roots not yet completed
+    kc_result* early;           // nullable: each query's result as soon as it completes (by slot)
+    unsigned* done;             // with early: set to 1 (after a system fence) once early[slot] is written
 };
+
+// a query's result from its accumulators; `complete`: every root finished
+__device__ __forceinline__ kc_result compose_result(const QDesc& D, const unsigned long long* out3, bool complete) {
+    kc_result r;
+    r.total = 0;
+    r.total_hi = 0;
+    r.flags = 0;
+    r.status = KC_OK;
+    r.words = 0;
+    if (D.k == 1) {
+        r.total = D.n;
+    } else if (D.k == 2) {
+        r.total = D.m;
+    } else if (D.k <= D.d_max + 1) {
+        r.total = *(volatile const unsigned long long*)&out3[0];
+        r.total_hi = *(volatile const unsigned long long*)&out3[1];
+        r.words = *(volatile const unsigned long long*)&out3[2];
+        if (r.total_hi) r.flags |= KC_FLAG_TOTAL_OVERFLOW;
+    }
+    if (!complete) {
+        r.flags |= KC_FLAG_TIMEOUT;
+        r.status = KC_E_TIMEOUT;
+    }
+    return r;
+}
+
+// publish query q's result early (one thread; every contribution is in out)
+__device__ __forceinline__ void publish_early(const BatchParams& B, uint32_t q) {
+    const QDesc& D = B.q[q];
+    __threadfence();
+    B.early[D.slot] = compose_result(D, B.out + 3 * (size_t)q, true);
+    __threadfence_system();
+    *(volatile unsigned*)&B.done[D.slot] = 1u;
+}
+
+// `n` more roots of query q are complete (one thread, after their counts
+// were added to out)
+__device__ __forceinline__ void complete_roots(const BatchParams& B, uint32_t q, uint32_t n) {
+    if (n == 0) return;
+    __threadfence();
+    if (atomicSub(&B.remaining[q], n) == n && B.early) publish_early(B, q);
+}
 
 // the query whose item range [pre[q], pre[q + 1]) holds item i (i < pre[nq])
 __device__ __forceinline__ uint32_t find_query(const uint32_t* pre, uint32_t nq, uint32_t i) {
@@ -1051,17 +1096,22 @@ __device__ __forceinline__ uint32_t roots_at_least(const uint32_t* rp, const uin
     return lo;
 }
 
-__global__ void k_batch_prep(const QDesc* __restrict__ q, uint32_t nq, uint32_t* __restrict__ nbig,
-                             uint32_t* __restrict__ nwork) {
+__global__ void k_batch_prep(const BatchParams B, uint32_t* __restrict__ nwork) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nq) return;
-    const QDesc D = q[i];
+    if (i >= B.nq) return;
+    const QDesc D = B.q[i];
+    uint32_t* nbig = const_cast<uint32_t*>(B.nbig);
     if (D.k < 3 || D.k > D.d_max + 1) {
         nbig[i] = nwork[i] = 0;
+        B.remaining[i] = 0;
+        if (B.early) publish_early(B, i);  // nothing to traverse
         return;
     }
-    nwork[i] = roots_at_least(D.rp, D.roots, D.n_roots, D.k - 1);
+    const uint32_t w = roots_at_least(D.rp, D.roots, D.n_roots, D.k - 1);
+    nwork[i] = w;
     nbig[i] = roots_at_least(D.rp, D.roots, D.n_roots, max(D.k - 1, (uint32_t)SMALL_D + 1));
+    B.remaining[i] = w;
+    if (w == 0 && B.early) publish_early(B, i);
 }
 
 // exclusive prefix sums of nbig and of nwork - nbig (one block of 1024)
@@ -1118,15 +1168,11 @@ __global__ void __launch_bounds__(1024) k_batch_scan(const uint32_t* __restrict_
     }
 }
 
+// Big roots of a batched launch, one per block, until none is left.
 template <int G, bool EC>
-__global__ void __launch_bounds__(BLOCK) k_count_batch(const BatchParams B) {
-    extern __shared__ __align__(16) uint32_t smem[];
-    __shared__ BlockShared sh;
-    __shared__ StealShared ss;
-    __shared__ uint32_t s_q, s_u;
+__device__ void batch_big(const BatchParams& B, uint32_t* smem, BlockShared& sh, StealShared& ss, uint32_t* s_qu,
+                          Acc& acc) {
     const uint32_t nbig_total = B.big_pre[B.nq];
-    const uint32_t nsmall_total = B.small_pre[B.nq];
-    Acc acc;
     while (nbig_total) {
         if (threadIdx.x == 0) {
             const uint32_t i = timed_out(B.base.ctl) ? NONE : atomicAdd(&B.bc->big_cursor, 1u);
@@ -1135,70 +1181,100 @@ __global__ void __launch_bounds__(BLOCK) k_count_batch(const BatchParams B) {
                 q = find_query(B.big_pre, B.nq, i);
                 u = B.q[q].roots[i - B.big_pre[q]];
             }
-            s_q = q;
-            s_u = u;
+            s_qu[0] = q;
+            s_qu[1] = u;
             sh.task = 0;
         }
         __syncthreads();
-        const uint32_t q = s_q;
+        const uint32_t q = s_qu[0];
         if (q == NONE) break;
         const QDesc* D = B.q + q;
-        block_root<G, EC>(B.base, D->rp, D->col, D->k, 0, s_u, smem, sh, ss, acc);
+        block_root<G, EC>(B.base, D->rp, D->col, D->k, 0, s_qu[1], smem, sh, ss, acc);
         flush_warp_acc(acc, B.out + 3 * (size_t)q);
         __syncthreads();
+        if (threadIdx.x == 0 && !timed_out(B.base.ctl)) complete_roots(B, q, 1);
     }
     __syncthreads();
+}
+
+// Small roots of a batched launch, one per warp, `chunk` per claim.
+__device__ void batch_small(const BatchParams& B, uint32_t* smem, Acc& acc) {
+    const uint32_t nsmall_total = B.small_pre[B.nq];
     if (nsmall_total == 0) return;
     WarpShared* ws = reinterpret_cast<WarpShared*>(smem) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     uint32_t cur = NONE, lo = 0, hi = 0;  // the current query and its item range
+    uint32_t finished = 0;                 // roots of cur completed since its last flush
     for (;;) {
         uint32_t j = 0;
         if (lane == 0) j = timed_out(B.base.ctl) ? NONE : atomicAdd(&B.bc->small_cursor, B.chunk);
         j = __shfl_sync(0xffffffffu, j, 0);
         if (j >= nsmall_total) break;
         const uint32_t j1 = min(j + B.chunk, nsmall_total);
+        bool stop = false;
         for (uint32_t t = j; t < j1; ++t) {
             if (t < lo || t >= hi) {
                 const uint32_t q = find_query(B.small_pre, B.nq, t);
-                if (cur != NONE) flush_warp_acc(acc, B.out + 3 * (size_t)cur);
+                if (cur != NONE) {
+                    flush_warp_acc(acc, B.out + 3 * (size_t)cur);
+                    if (lane == 0) complete_roots(B, cur, finished);
+                }
+                finished = 0;
                 cur = q;
                 lo = B.small_pre[q];
                 hi = B.small_pre[q + 1];
             }
             const QDesc* D = B.q + cur;
             warp_root(B.base, D->rp, D->col, D->k, D->roots[B.nbig[cur] + (t - lo)], *ws, acc);
+            int to = 0;
+            if (lane == 0) to = timed_out(B.base.ctl);
+            if (__shfl_sync(0xffffffffu, to, 0)) {
+                stop = true;
+                break;
+            }
+            ++finished;
+        }
+        if (stop) break;
+        // a query whose last roots this warp holds is published without waiting
+        // for the warp's next claim
+        if (cur != NONE && finished && hi <= j1) {
+            flush_warp_acc(acc, B.out + 3 * (size_t)cur);
+            if (lane == 0) complete_roots(B, cur, finished);
+            finished = 0;
         }
     }
-    if (cur != NONE) flush_warp_acc(acc, B.out + 3 * (size_t)cur);
+    if (cur != NONE) {
+        flush_warp_acc(acc, B.out + 3 * (size_t)cur);
+        if (lane == 0 && !timed_out(B.base.ctl)) complete_roots(B, cur, finished);
+    }
+}
+
+// Odd blocks take the small roots first and even blocks the big ones, so
+// that neither kind waits for the other; queries are ordered cheapest first
+// by the host, so light queries complete early in both phases.
+template <int G, bool EC>
+__global__ void __launch_bounds__(BLOCK) k_count_batch(const BatchParams B) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ BlockShared sh;
+    __shared__ StealShared ss;
+    __shared__ uint32_t s_qu[2];
+    Acc acc;
+    if (blockIdx.x & 1) {
+        batch_small(B, smem, acc);
+        __syncthreads();
+        batch_big<G, EC>(B, smem, sh, ss, s_qu, acc);
+    } else {
+        batch_big<G, EC>(B, smem, sh, ss, s_qu, acc);
+        batch_small(B, smem, acc);
+    }
 }
 
 __global__ void k_batch_finalize(const QDesc* __restrict__ q, uint32_t nq, const unsigned long long* __restrict__ out,
-                                 const Ctl* ctl, kc_result* __restrict__ res) {
+                                 const unsigned* __restrict__ remaining, kc_result* __restrict__ res) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nq) return;
     const QDesc D = q[i];
-    kc_result r;
-    r.total = 0;
-    r.total_hi = 0;
-    r.flags = 0;
-    r.status = KC_OK;
-    r.words = 0;
-    if (D.k == 1) {
-        r.total = D.n;
-    } else if (D.k == 2) {
-        r.total = D.m;
-    } else if (D.k <= D.d_max + 1) {
-        r.total = out[3 * (size_t)i];
-        r.total_hi = out[3 * (size_t)i + 1];
-        r.words = out[3 * (size_t)i + 2];
-        if (r.total_hi) r.flags |= KC_FLAG_TOTAL_OVERFLOW;
-    }
-    if (ctl->flags & KC_FLAG_TIMEOUT) {
-        r.flags |= KC_FLAG_TIMEOUT;
-        r.status = KC_E_TIMEOUT;
-    }
-    res[D.slot] = r;
+    res[D.slot] = compose_result(D, out + 3 * (size_t)i, remaining[i] == 0);
 }
 
 typedef void (*BatchKernel)(const BatchParams);
@@ -1218,7 +1294,7 @@ static BatchKernel pick_batch(uint32_t G) {
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 size_t batch_ws_bytes(uint32_t nq) {
-    return al256(sizeof(Ctl) + sizeof(BatchCtl)) + 4 * al256(((size_t)nq + 1) * 4) + al256((size_t)nq * 24 + 8);
+    return al256(sizeof(Ctl) + sizeof(BatchCtl)) + 5 * al256(((size_t)nq + 1) * 4) + al256((size_t)nq * 24 + 8);
 }
 
 size_t batch_smem_bytes(uint32_t d_cap, uint32_t k_max, const BatchConfig& cfg) {
@@ -1228,30 +1304,46 @@ size_t batch_smem_bytes(uint32_t d_cap, uint32_t k_max, const BatchConfig& cfg) 
 }
 
 kc_status batch_launch(const QDesc* q_dev, uint32_t nq, uint32_t d_cap, uint32_t k_max, const BatchConfig& cfg,
-                       void* ws, double time_limit_s, int sm_count, kc_result* results_dev, cudaStream_t s) {
+                       void* ws, double time_limit_s, int sm_count, kc_result* results_dev, kc_result* early,
+                       unsigned* done, cudaStream_t s) {
     if (nq == 0) return KC_OK;
     const uint32_t G = cfg.subwarp;
     if (G != 1 && G != 2 && G != 4 && G != 8 && G != 16 && G != 32)
         return set_error(KC_E_INVALID_ARG, "subwarp must be 1, 2, 4, 8, 16 or 32");
     if (k_max > MAX_DEPTH + 4)
         return set_error(KC_E_UNSUPPORTED, "orientation traversal supports k <= %d", MAX_DEPTH + 4);
+    if ((early == nullptr) != (done == nullptr)) return set_error(KC_E_INVALID_ARG, "early and done go together");
     char* p = (char*)ws;
     Ctl* ctl = (Ctl*)p;
     BatchCtl* bc = (BatchCtl*)(ctl + 1);
     p += al256(sizeof(Ctl) + sizeof(BatchCtl));
-    uint32_t* nbig = (uint32_t*)p;
-    p += al256(((size_t)nq + 1) * 4);
-    uint32_t* nwork = (uint32_t*)p;
-    p += al256(((size_t)nq + 1) * 4);
-    uint32_t* big_pre = (uint32_t*)p;
-    p += al256(((size_t)nq + 1) * 4);
-    uint32_t* small_pre = (uint32_t*)p;
-    p += al256(((size_t)nq + 1) * 4);
+    uint32_t* arr[5];
+    for (int i = 0; i < 5; ++i) {
+        arr[i] = (uint32_t*)p;
+        p += al256(((size_t)nq + 1) * 4);
+    }
+    uint32_t *nbig = arr[0], *nwork = arr[1], *big_pre = arr[2], *small_pre = arr[3], *remaining = arr[4];
     unsigned long long* out = (unsigned long long*)p;
     KC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl) + sizeof(BatchCtl), s));
     KC_CUDA(cudaMemsetAsync(out, 0, (size_t)nq * 24, s));
+    BatchParams B;
+    memset(&B, 0, sizeof(B));
+    B.base.ctl = ctl;
+    B.base.help_min = 0;
+    B.base.in_smem = 1;
+    B.q = q_dev;
+    B.nq = nq;
+    B.chunk = std::max<uint32_t>(cfg.chunk, 1);
+    B.nbig = nbig;
+    B.big_pre = big_pre;
+    B.small_pre = small_pre;
+    B.out = out;
+    B.bc = bc;
+    B.remaining = remaining;
+    B.early = early;
+    B.done = done;
     const unsigned qb = (nq + 255) / 256;
-    k_batch_prep<<<qb, 256, 0, s>>>(q_dev, nq, nbig, nwork);
+    k_batch_prep<<<qb, 256, 0, s>>>(B, nwork);
     note_launch();
     k_batch_scan<<<1, 1024, 0, s>>>(nbig, nwork, nq, big_pre, small_pre);
     note_launch();
@@ -1270,28 +1362,15 @@ kc_status batch_launch(const QDesc* q_dev, uint32_t nq, uint32_t d_cap, uint32_t
         int bps = 0;
         KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, BLOCK, geo.smem_bytes));
         if (bps < 1) return set_error(KC_E_UNSUPPORTED, "batch kernel cannot be resident (smem %zu)", geo.smem_bytes);
-        BatchParams B;
-        memset(&B, 0, sizeof(B));
         B.base.dcap = geo.dcap;
         B.base.wcap = geo.wcap;
         B.base.depth = geo.depth;
-        B.base.in_smem = 1;
         B.base.hash_words = geo.hash_words;
-        B.base.help_min = 0;
-        B.base.ctl = ctl;
-        B.q = q_dev;
-        B.nq = nq;
-        B.chunk = std::max<uint32_t>(cfg.chunk, 1);
-        B.nbig = nbig;
-        B.big_pre = big_pre;
-        B.small_pre = small_pre;
-        B.out = out;
-        B.bc = bc;
         kern<<<bps * sm_count, BLOCK, geo.smem_bytes, s>>>(B);
         note_launch();
         KC_CUDA(cudaGetLastError());
     }
-    k_batch_finalize<<<qb, 256, 0, s>>>(q_dev, nq, out, ctl, results_dev);
+    k_batch_finalize<<<qb, 256, 0, s>>>(q_dev, nq, out, remaining, results_dev);
     note_launch();
     KC_CUDA(cudaGetLastError());
     return KC_OK;

@@ -1,0 +1,506 @@
+// Serving loop (include/kclique.h, kc_server_*): a pool of resident oriented
+// graphs and a worker thread that admits count queries as they arrive.
+//
+// Orientation-mode queries (pivot = 0) whose graphs fit the batched kernel
+// wait in one queue; whenever one of the batch slots (a stream with its own
+// working memory) is free, the worker packs up to max_batch of them into one
+// persistent launch (batch_launch), so queries that arrive while others run
+// start on the next free slot and their launches overlap on the device.
+// Each query's result is published to host-mapped memory by the thread that
+// completes its last root, so it is served before the rest of its launch
+// ends.  Persistent launches hold their SMs until done, so every batch slot
+// and the graph path launch on a fixed share of the SMs (SMs / (slots + 1))
+// and a long launch cannot starve the others.  Pivot queries, and orientation queries whose bitmaps need global
+// memory, run one at a time through the graph's own path (kc_count_async).
+// A query is admitted while the server's resident bytes stay within its
+// device-memory budget and the device reports that much memory free.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "kc_common.cuh"
+
+namespace kc {
+namespace srv {
+
+using Clock = std::chrono::steady_clock;
+
+struct Ticket {
+    uint32_t graph = 0, k = 0;
+    int pivot = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    kc_result r{};
+    int state = 0;  // 0 queued, 1 running, 2 done
+    uint32_t launch = 0;
+};
+
+struct BatchSlot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    DevBuf ws;                    // descriptors, then every group's working memory
+    DevBuf res;                   // final results of the launch
+    kc_result* res_h = nullptr;   // pinned copy of res
+    kc_result* early_h = nullptr; // mapped: results published early
+    unsigned* done_h = nullptr;   // mapped: 1 once early_h[i] is written
+    kc_result* early_d = nullptr;
+    unsigned* done_d = nullptr;
+    QDesc* stage = nullptr;       // pinned descriptors
+    std::vector<uint64_t> tickets;
+    std::vector<char> finished;
+    bool busy = false;
+};
+
+struct SingleSlot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    DevBuf res;
+    kc_result* res_h = nullptr;
+    uint64_t ticket = 0;
+    bool busy = false;
+};
+
+static constexpr uint32_t MAX_GROUPS = 16;
+
+static size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static size_t batch_slot_bytes(uint32_t cap) {
+    return al((size_t)cap * sizeof(QDesc)) + MAX_GROUPS * al(batch_ws_bytes(cap));
+}
+
+}  // namespace srv
+}  // namespace kc
+
+using namespace kc;
+using namespace kc::srv;
+
+struct kc_server {
+    int device = 0;
+    int sms = 0;
+    int share = 0;        // SMs' worth of blocks per launch: every slot's launches fit side by side
+    size_t budget = 0;
+    size_t resident = 0;
+    uint32_t max_batch = 1;
+    int flags = 0;
+    double time_limit = 0;
+    std::vector<kc_graph*> graphs;
+    std::deque<Ticket> tickets;
+    std::deque<uint64_t> q_batch, q_single;
+    std::vector<BatchSlot> bs;
+    SingleSlot ss;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread worker;
+    bool stop = false;
+    Clock::time_point t0;
+    uint64_t launches = 0, served = 0;
+    cudaStream_t setup = nullptr;
+
+    double now_ms() const { return std::chrono::duration<double, std::milli>(Clock::now() - t0).count(); }
+};
+
+namespace {
+
+// Launch configuration of a query (the paper's guideline, Section 4.5).
+BatchConfig config_of(uint32_t d_max, uint32_t k) {
+    BatchConfig c;
+    c.ec = k >= 6;
+    c.subwarp = ((d_max + 31) / 32) <= 8 ? 4 : 8;
+    c.chunk = 16;
+    return c;
+}
+
+bool batchable(const kc_graph* g, uint32_t k, int pivot) {
+    if (pivot) return false;
+    if (k < 3 || k > g->d_max + 1) return true;
+    if (k > 68) return false;
+    return batch_smem_bytes(g->d_max, k, config_of(g->d_max, k)) != 0;
+}
+
+void finish(kc_server* S, uint64_t t, const kc_result& r) {
+    Ticket& T = S->tickets[t];
+    T.r = r;
+    T.t_done = S->now_ms();
+    T.state = 2;
+    S->served++;
+}
+
+kc_result error_result(kc_status st) {
+    kc_result r{};
+    r.status = st;
+    return r;
+}
+
+// Pack up to max_batch queued orientation queries into one launch on slot b.
+void launch_batch(kc_server* S, BatchSlot& b) {
+    const uint32_t n = (uint32_t)std::min<size_t>(S->q_batch.size(), S->max_batch);
+    b.tickets.assign(S->q_batch.begin(), S->q_batch.begin() + n);
+    S->q_batch.erase(S->q_batch.begin(), S->q_batch.begin() + n);
+    b.finished.assign(n, 0);
+    // descriptors grouped by configuration
+    struct Item {
+        BatchConfig c;
+        double cost;
+        uint32_t i;
+    };
+    std::vector<Item> items(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        const Ticket& T = S->tickets[b.tickets[i]];
+        const kc_graph* g = S->graphs[T.graph];
+        items[i].c = config_of(g->d_max, T.k);
+        items[i].cost = query_cost_estimate(g->m, g->d_max, T.k);
+        items[i].i = i;
+    }
+    auto key = [](const BatchConfig& c) { return (c.ec << 20) | (c.subwarp << 8) | c.chunk; };
+    // one launch per configuration; inside one, cheapest queries first
+    std::stable_sort(items.begin(), items.end(), [&](const Item& x, const Item& y) {
+        return key(x.c) != key(y.c) ? key(x.c) < key(y.c) : x.cost < y.cost;
+    });
+    struct Grp {
+        BatchConfig c;
+        uint32_t first, count, d_cap, k_max;
+    };
+    std::vector<Grp> groups;
+    for (uint32_t j = 0; j < n; ++j) {
+        const Ticket& T = S->tickets[b.tickets[items[j].i]];
+        const kc_graph* g = S->graphs[T.graph];
+        QDesc& D = b.stage[j];
+        D.rp = (const uint32_t*)g->row_ptr.ptr;
+        D.col = (const uint32_t*)g->col.ptr;
+        D.roots = (const uint32_t*)g->roots.ptr;
+        D.n_roots = g->n;
+        D.k = T.k;
+        D.n = g->n;
+        D.d_max = g->d_max;
+        D.m = g->m;
+        D.slot = items[j].i;
+        D.pad = 0;
+        // config_of yields at most four configurations (<= MAX_GROUPS)
+        if (groups.empty() || key(groups.back().c) != key(items[j].c)) groups.push_back({items[j].c, j, 0, 0, 0});
+        Grp& G = groups.back();
+        G.count++;
+        if (T.k >= 3 && T.k <= g->d_max + 1) {
+            G.d_cap = std::max(G.d_cap, g->d_max);
+            G.k_max = std::max(G.k_max, T.k);
+        }
+    }
+    const uint32_t used = n;
+    const double now = S->now_ms();
+    const uint32_t launch = (uint32_t)++S->launches;
+    for (uint32_t j = 0; j < used; ++j) {
+        Ticket& T = S->tickets[b.tickets[items[j].i]];
+        T.state = 1;
+        T.t_admit = now;
+        T.launch = launch;
+    }
+    memset(b.done_h, 0, (size_t)S->max_batch * 4);
+    kc_status st = KC_OK;
+    cudaError_t e = cudaMemcpyAsync(b.ws.ptr, b.stage, (size_t)used * sizeof(QDesc), cudaMemcpyHostToDevice, b.st);
+    if (e != cudaSuccess) st = cuda_error(e, "descriptors", __FILE__, __LINE__);
+    const QDesc* qd = (const QDesc*)b.ws.ptr;
+    char* ws = (char*)b.ws.ptr + al((size_t)S->max_batch * sizeof(QDesc));
+    for (size_t gi = 0; gi < groups.size() && st == KC_OK; ++gi) {
+        const Grp& G = groups[gi];
+        st = batch_launch(qd + G.first, G.count, G.d_cap, G.k_max, G.c, ws + gi * al(batch_ws_bytes(S->max_batch)),
+                          S->time_limit, S->share, (kc_result*)b.res.ptr, b.early_d, b.done_d, b.st);
+    }
+    if (st == KC_OK) {
+        e = cudaMemcpyAsync(b.res_h, b.res.ptr, (size_t)n * sizeof(kc_result), cudaMemcpyDeviceToHost, b.st);
+        if (e == cudaSuccess) e = cudaEventRecord(b.ev, b.st);
+        if (e != cudaSuccess) st = cuda_error(e, "batch results", __FILE__, __LINE__);
+    }
+    if (st != KC_OK) {
+        cudaStreamSynchronize(b.st);
+        for (uint32_t j = 0; j < used; ++j) finish(S, b.tickets[items[j].i], error_result(st));
+        b.tickets.clear();
+        return;
+    }
+    b.busy = true;  // result slot i <-> b.tickets[i]
+}
+
+void launch_single(kc_server* S) {
+    const uint64_t t = S->q_single.front();
+    S->q_single.pop_front();
+    Ticket& T = S->tickets[t];
+    kc_graph* g = S->graphs[T.graph];
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    if (fr < ((size_t)256 << 20)) {  // too little free device memory for the pivot path's buffers
+        finish(S, t, error_result(KC_E_NO_MEMORY));
+        return;
+    }
+    T.state = 1;
+    T.t_admit = S->now_ms();
+    T.launch = (uint32_t)++S->launches;
+    kc_status st = kc_count_async(g, T.k, T.pivot, KC_SCHEME_AUTO, 0, (kc_result*)S->ss.res.ptr, nullptr, S->ss.st);
+    if (st == KC_OK) {
+        cudaError_t e = cudaMemcpyAsync(S->ss.res_h, S->ss.res.ptr, sizeof(kc_result), cudaMemcpyDeviceToHost, S->ss.st);
+        if (e == cudaSuccess) e = cudaEventRecord(S->ss.ev, S->ss.st);
+        if (e != cudaSuccess) st = cuda_error(e, "single result", __FILE__, __LINE__);
+    }
+    if (st != KC_OK) {
+        cudaStreamSynchronize(S->ss.st);
+        finish(S, t, error_result(st));
+        return;
+    }
+    S->ss.ticket = t;
+    S->ss.busy = true;
+}
+
+void worker_main(kc_server* S) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        bool progress = false, busy = false;
+        for (BatchSlot& b : S->bs) {
+            if (!b.busy) continue;
+            for (size_t i = 0; i < b.tickets.size(); ++i)
+                if (!b.finished[i] && *(volatile unsigned*)&b.done_h[i]) {
+                    kc_result r;
+                    memcpy(&r, (const void*)&b.early_h[i], sizeof(r));
+                    finish(S, b.tickets[i], r);
+                    b.finished[i] = 1;
+                    progress = true;
+                }
+            if (cudaEventQuery(b.ev) == cudaSuccess) {
+                for (size_t i = 0; i < b.tickets.size(); ++i)
+                    if (!b.finished[i]) finish(S, b.tickets[i], b.res_h[i]);
+                b.busy = false;
+                progress = true;
+            } else {
+                busy = true;
+            }
+        }
+        if (S->ss.busy) {
+            if (cudaEventQuery(S->ss.ev) == cudaSuccess) {
+                finish(S, S->ss.ticket, *S->ss.res_h);
+                S->ss.busy = false;
+                progress = true;
+            } else {
+                busy = true;
+            }
+        }
+        if (progress) S->cv_done.notify_all();
+        const bool serial = (S->flags & KC_SERVER_SERIAL) != 0;
+        bool any_busy = S->ss.busy;
+        for (BatchSlot& b : S->bs) any_busy = any_busy || b.busy;
+        if (!(serial && any_busy)) {
+            // one single-path query at a time; in serial mode the oldest query goes first
+            bool single_first = !S->q_single.empty() &&
+                                (S->q_batch.empty() || S->q_single.front() < S->q_batch.front());
+            if (!S->ss.busy && !S->q_single.empty() && (!serial || single_first)) {
+                launch_single(S);
+                progress = true;
+            } else {
+                for (BatchSlot& b : S->bs) {
+                    if (b.busy || S->q_batch.empty()) continue;
+                    if (serial && any_busy) break;
+                    launch_batch(S, b);
+                    progress = true;
+                    any_busy = true;
+                    if (serial) break;
+                }
+            }
+        }
+        if (progress) continue;
+        if (busy || S->ss.busy) {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            lk.lock();
+        } else {
+            S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+        }
+    }
+}
+
+void free_slot(BatchSlot& b) {
+    if (b.st) cudaStreamSynchronize(b.st);
+    if (b.ev) cudaEventDestroy(b.ev);
+    if (b.st) cudaStreamDestroy(b.st);
+    dev_free(b.ws);
+    dev_free(b.res);
+    if (b.res_h) cudaFreeHost(b.res_h);
+    if (b.early_h) cudaFreeHost(b.early_h);
+    if (b.done_h) cudaFreeHost(b.done_h);
+    if (b.stage) cudaFreeHost(b.stage);
+}
+
+}  // namespace
+
+extern "C" {
+
+kc_status kc_server_create(size_t hbm_budget, uint32_t max_batch, uint32_t slots, int flags, kc_server** out) {
+    clear_error();
+    if (!out) return set_error(KC_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (max_batch == 0 || slots == 0) return set_error(KC_E_INVALID_ARG, "max_batch and slots must be >= 1");
+    if (flags & ~KC_SERVER_SERIAL) return set_error(KC_E_INVALID_ARG, "unknown flags %d", flags);
+    kc_server* S = new (std::nothrow) kc_server();
+    if (!S) return set_error(KC_E_NO_MEMORY, "host allocation failed");
+    S->flags = flags;
+    S->max_batch = (flags & KC_SERVER_SERIAL) ? 1 : max_batch;
+    if (flags & KC_SERVER_SERIAL) slots = 1;
+    S->budget = hbm_budget;
+    S->t0 = Clock::now();
+    cudaGetDevice(&S->device);
+    S->sms = sm_count_of_current_device();
+    // persistent launches keep their SMs until their work is done, so each
+    // batch slot and the graph path get a fixed share (all of it when serial)
+    S->share = (flags & KC_SERVER_SERIAL) ? S->sms : std::max(1, S->sms / (int)(slots + 1));
+    auto fail = [&](kc_status st) {
+        kc_server_destroy(S);
+        return st;
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&S->setup, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail(cuda_error(e, "stream", __FILE__, __LINE__));
+    S->bs.resize(slots);
+    for (BatchSlot& b : S->bs) {
+        e = cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaHostAlloc((void**)&b.res_h, (size_t)S->max_batch * sizeof(kc_result), 0);
+        if (e == cudaSuccess)
+            e = cudaHostAlloc((void**)&b.early_h, (size_t)S->max_batch * sizeof(kc_result), cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostAlloc((void**)&b.done_h, (size_t)S->max_batch * 4, cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostAlloc((void**)&b.stage, (size_t)S->max_batch * sizeof(QDesc), 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&b.early_d, b.early_h, 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&b.done_d, b.done_h, 0);
+        if (e != cudaSuccess) return fail(cuda_error(e, "batch slot", __FILE__, __LINE__));
+        kc_status st = dev_alloc(b.ws, batch_slot_bytes(S->max_batch));
+        if (st == KC_OK) st = dev_alloc(b.res, (size_t)S->max_batch * sizeof(kc_result));
+        if (st != KC_OK) return fail(st);
+        S->resident += b.ws.bytes + b.res.bytes;
+    }
+    e = cudaStreamCreateWithFlags(&S->ss.st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ss.ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&S->ss.res_h, sizeof(kc_result), 0);
+    if (e != cudaSuccess) return fail(cuda_error(e, "single slot", __FILE__, __LINE__));
+    kc_status st = dev_alloc(S->ss.res, sizeof(kc_result) + 64);
+    if (st != KC_OK) return fail(st);
+    if (S->resident > S->budget)
+        return fail(set_error(KC_E_NO_MEMORY, "the slots alone (%zu bytes) exceed the budget", S->resident));
+    S->worker = std::thread(worker_main, S);
+    *out = S;
+    return KC_OK;
+}
+
+kc_status kc_server_add_graph(kc_server* S, const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n,
+                              uint64_t nnz, int ptrs_on_device, int orient, int validate, uint32_t* graph_id) {
+    clear_error();
+    if (!S || !graph_id) return set_error(KC_E_INVALID_ARG, "NULL server or graph_id");
+    kc_graph* g = nullptr;
+    KC_CHECK(kc_graph_create(row_ptr, col_idx, n, nnz, ptrs_on_device, orient, validate, S->setup, &g));
+    kc_graph_info info;
+    kc_graph_info_get(g, &info);
+    std::lock_guard<std::mutex> lk(S->mu);
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    if (S->resident + info.device_bytes > S->budget) {
+        kc_graph_destroy(g);
+        return set_error(KC_E_NO_MEMORY, "graph of %llu bytes exceeds the server budget",
+                         (unsigned long long)info.device_bytes);
+    }
+    kc_graph_set_time_limit(g, S->time_limit);
+    g->sm_count = S->share;  // launches of the graph path take one share too
+    S->resident += info.device_bytes;
+    *graph_id = (uint32_t)S->graphs.size();
+    S->graphs.push_back(g);
+    return KC_OK;
+}
+
+kc_status kc_server_set_time_limit(kc_server* S, double seconds) {
+    clear_error();
+    if (!S) return set_error(KC_E_INVALID_ARG, "NULL server");
+    if (!(seconds >= 0)) return set_error(KC_E_INVALID_ARG, "time limit must be >= 0");
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->time_limit = seconds;
+    for (kc_graph* g : S->graphs) kc_graph_set_time_limit(g, seconds);
+    return KC_OK;
+}
+
+kc_status kc_server_submit(kc_server* S, uint32_t graph_id, uint32_t k, int pivot, uint64_t* ticket) {
+    clear_error();
+    if (!S || !ticket) return set_error(KC_E_INVALID_ARG, "NULL server or ticket");
+    if (k == 0) return set_error(KC_E_INVALID_ARG, "k must be >= 1");
+    if (pivot != 0 && pivot != 1) return set_error(KC_E_INVALID_ARG, "pivot must be 0 or 1");
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (graph_id >= S->graphs.size()) return set_error(KC_E_INVALID_ARG, "unknown graph %u", graph_id);
+    Ticket T;
+    T.graph = graph_id;
+    T.k = k;
+    T.pivot = pivot;
+    T.t_submit = S->now_ms();
+    const uint64_t id = S->tickets.size();
+    S->tickets.push_back(T);
+    if (batchable(S->graphs[graph_id], k, pivot))
+        S->q_batch.push_back(id);
+    else
+        S->q_single.push_back(id);
+    *ticket = id;
+    S->cv_work.notify_one();
+    return KC_OK;
+}
+
+kc_status kc_server_poll(kc_server* S, uint64_t ticket, kc_server_result* out, int timeout_ms) {
+    clear_error();
+    if (!S || !out) return set_error(KC_E_INVALID_ARG, "NULL server or out");
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (ticket >= S->tickets.size()) return set_error(KC_E_INVALID_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    auto ready = [&] { return S->tickets[ticket].state == 2; };
+    if (timeout_ms < 0)
+        S->cv_done.wait(lk, ready);
+    else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+        return set_error(KC_E_TIMEOUT, "ticket %llu not finished yet", (unsigned long long)ticket);
+    const Ticket& T = S->tickets[ticket];
+    out->total = T.r.total;
+    out->total_hi = T.r.total_hi;
+    out->flags = T.r.flags;
+    out->status = T.r.status;
+    out->graph_id = T.graph;
+    out->k = T.k;
+    out->pivot = T.pivot;
+    out->launch = T.launch;
+    out->t_submit_ms = T.t_submit;
+    out->t_admit_ms = T.t_admit;
+    out->t_done_ms = T.t_done;
+    return KC_OK;
+}
+
+kc_status kc_server_stats(kc_server* S, uint64_t* launches, uint64_t* served, uint64_t* resident_bytes) {
+    clear_error();
+    if (!S) return set_error(KC_E_INVALID_ARG, "NULL server");
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (launches) *launches = S->launches;
+    if (served) *served = S->served;
+    if (resident_bytes) *resident_bytes = S->resident;
+    return KC_OK;
+}
+
+kc_status kc_server_destroy(kc_server* S) {
+    if (!S) return KC_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    for (BatchSlot& b : S->bs) free_slot(b);
+    if (S->ss.st) cudaStreamSynchronize(S->ss.st);
+    if (S->ss.ev) cudaEventDestroy(S->ss.ev);
+    if (S->ss.st) cudaStreamDestroy(S->ss.st);
+    dev_free(S->ss.res);
+    if (S->ss.res_h) cudaFreeHost(S->ss.res_h);
+    for (kc_graph* g : S->graphs) kc_graph_destroy(g);
+    if (S->setup) cudaStreamDestroy(S->setup);
+    delete S;
+    return KC_OK;
+}
+
+}  // extern "C"

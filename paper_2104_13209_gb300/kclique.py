@@ -48,7 +48,11 @@ EXPORTED = [
     "kc_graph_set_time_limit", "kc_launch_count", "kc_graph_last_work",
     "kc_batch_create", "kc_batch_destroy", "kc_batch_graph_info", "kc_batch_set_time_limit", "kc_batch_count",
     "kc_batch_tune", "kc_batch_capture", "kc_batch_exec_launch", "kc_batch_exec_destroy",
+    "kc_server_create", "kc_server_add_graph", "kc_server_set_time_limit", "kc_server_submit", "kc_server_poll",
+    "kc_server_stats", "kc_server_destroy",
 ]
+
+KC_SERVER_SERIAL = 1
 
 
 class kc_graph_info(ctypes.Structure):
@@ -60,6 +64,13 @@ class kc_graph_info(ctypes.Structure):
 class kc_result(ctypes.Structure):
     _fields_ = [("total", ctypes.c_uint64), ("total_hi", ctypes.c_uint64), ("flags", ctypes.c_uint32),
                 ("status", ctypes.c_uint32), ("words", ctypes.c_uint64)]
+
+
+class kc_server_result(ctypes.Structure):
+    _fields_ = [("total", ctypes.c_uint64), ("total_hi", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+                ("status", ctypes.c_int32), ("graph_id", ctypes.c_uint32), ("k", ctypes.c_uint32),
+                ("pivot", ctypes.c_int32), ("launch", ctypes.c_uint32), ("t_submit_ms", ctypes.c_double),
+                ("t_admit_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double)]
 
 
 KC_TUNE_MAX = 256
@@ -133,6 +144,16 @@ def load(build_if_missing: bool = False):
     lib.kc_batch_capture.argtypes = [vp, vp, vp, u32, vp, vp, ctypes.POINTER(vp)]
     lib.kc_batch_exec_launch.argtypes = [vp, vp]
     lib.kc_batch_exec_destroy.argtypes = [vp]
+    lib.kc_server_create.argtypes = [ctypes.c_size_t, u32, u32, i32, ctypes.POINTER(vp)]
+    lib.kc_server_add_graph.argtypes = [vp, vp, vp, u32, u64, i32, i32, i32, ctypes.POINTER(u32)]
+    lib.kc_server_set_time_limit.argtypes = [vp, ctypes.c_double]
+    lib.kc_server_submit.argtypes = [vp, u32, u32, i32, ctypes.POINTER(u64)]
+    lib.kc_server_poll.argtypes = [vp, u64, ctypes.POINTER(kc_server_result), i32]
+    lib.kc_server_stats.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]
+    lib.kc_server_destroy.argtypes = [vp]
+    for f in ("kc_server_create", "kc_server_add_graph", "kc_server_set_time_limit", "kc_server_submit",
+              "kc_server_poll", "kc_server_stats", "kc_server_destroy"):
+        getattr(lib, f).restype = i32
     for f in ("kc_batch_create", "kc_batch_destroy", "kc_batch_graph_info", "kc_batch_set_time_limit",
               "kc_batch_count", "kc_batch_tune", "kc_batch_capture", "kc_batch_exec_launch", "kc_batch_exec_destroy"):
         getattr(lib, f).restype = i32
@@ -415,6 +436,65 @@ class BatchExec:
     def close(self):
         if getattr(self, "_h", None):
             load().kc_batch_exec_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """A serving loop over resident graphs (kc_server_*): submit queries
+    (graph, k, pivot) from any thread, poll their results."""
+
+    def __init__(self, hbm_budget: int = 64 << 30, max_batch: int = 256, slots: int = 4, serial: bool = False):
+        h = ctypes.c_void_p()
+        _check(load().kc_server_create(hbm_budget, max_batch, slots, KC_SERVER_SERIAL if serial else 0,
+                                       ctypes.byref(h)))
+        self._h = h
+
+    def add_graph(self, g=None, row_ptr=None, col_idx=None, n=None, orient: str = "degeneracy",
+                  validate: bool = True) -> int:
+        if g is not None:
+            row_ptr, col_idx, n = g.row_ptr, g.col_idx, g.n
+        rp = np.ascontiguousarray(row_ptr, dtype=np.uint32)
+        ci = np.ascontiguousarray(col_idx, dtype=np.uint32)
+        if n is None:
+            n = rp.size - 1
+        gid = ctypes.c_uint32()
+        _check(load().kc_server_add_graph(self._h, rp.ctypes.data, ci.ctypes.data if ci.size else None, n, ci.size,
+                                          0, _ORIENT[orient], int(validate), ctypes.byref(gid)))
+        return gid.value
+
+    def set_time_limit(self, seconds: float):
+        _check(load().kc_server_set_time_limit(self._h, float(seconds)))
+
+    def submit(self, graph_id: int, k: int, pivot: bool = False) -> int:
+        t = ctypes.c_uint64()
+        _check(load().kc_server_submit(self._h, graph_id, k, int(pivot), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1) -> dict | None:
+        """The query's result (a dict), or None if it is not done within timeout_ms."""
+        r = kc_server_result()
+        st = load().kc_server_poll(self._h, ticket, ctypes.byref(r), timeout_ms)
+        if st == KC_E_TIMEOUT:
+            return None
+        _check(st)
+        return {"total": (r.total_hi << 64) | r.total, "flags": r.flags, "status": r.status, "graph": r.graph_id,
+                "k": r.k, "pivot": r.pivot, "launch": r.launch, "t_submit_ms": r.t_submit_ms,
+                "t_admit_ms": r.t_admit_ms, "t_done_ms": r.t_done_ms}
+
+    def stats(self) -> dict:
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().kc_server_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"launches": a.value, "served": b.value, "resident_bytes": c.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().kc_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

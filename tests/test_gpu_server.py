@@ -1,0 +1,105 @@
+"""The serving loop (kc_server_*): queries of different graphs, k and modes
+admitted while others run, batched on the fly -- each result equal to the
+CPU oracle's count, the same when the query runs alone and in the mix, and
+a query that runs out of time does not disturb the others."""
+import pytest
+
+from oracle import oracle as O
+from tests.gpu_common import kclique, lib, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def pool():
+    return [synth.erdos_renyi(2000, 0.01, 0), synth.rmat(12, 16, seed=1), synth.complete_graph(30),
+            synth.complete_multipartite([10] * 6), synth.dense_random_graph(100, 0.5, 3),
+            synth.chung_lu_planted(20000, 2.1, 10, 20, 20, 60, 0.9, seed=1)]
+
+
+def want(gs, g, k):
+    h = gs[g]
+    return h.n if k == 1 else (h.num_edges if k == 2 else O.count(h.row_ptr, h.col_idx, k))
+
+
+def queries(gs):
+    return [(g, k, p) for g in range(len(gs)) for k in (1, 2, 3, 4, 5, 7) for p in (0, 1)]
+
+
+def make_server(gs, **kw):
+    lib()
+    S = kclique.Server(**kw)
+    ids = [S.add_graph(h) for h in gs]
+    assert ids == list(range(len(gs)))
+    return S
+
+
+def wait(S, t):
+    r = S.poll(t, 120000)
+    assert r is not None, "query not served within two minutes"
+    return r
+
+
+def check(r, gs, g, k):
+    assert r["status"] == kclique.KC_OK and r["flags"] == 0, r
+    assert r["total"] == want(gs, g, k), (g, k, r)
+    assert r["t_submit_ms"] <= r["t_admit_ms"] <= r["t_done_ms"]
+
+
+def test_server_alone_and_mixed():
+    gs = pool()
+    qs = queries(gs)
+    S = make_server(gs, max_batch=64, slots=3)
+    alone = []
+    for g, k, p in qs:
+        r = wait(S, S.submit(g, k, bool(p)))
+        check(r, gs, g, k)
+        alone.append(r["total"])
+    tickets = [S.submit(g, k, bool(p)) for g, k, p in qs * 3]
+    mixed = [wait(S, t) for t in tickets]
+    for (g, k, p), r in zip(qs * 3, mixed):
+        check(r, gs, g, k)
+    assert [r["total"] for r in mixed] == alone * 3
+    st = S.stats()
+    assert st["served"] == 4 * len(qs) and st["launches"] <= st["served"]
+    S.close()
+
+
+def test_server_serial_baseline():
+    gs = pool()
+    qs = queries(gs)
+    S = make_server(gs, serial=True)
+    tickets = [S.submit(g, k, bool(p)) for g, k, p in qs]
+    for (g, k, p), t in zip(qs, tickets):
+        check(wait(S, t), gs, g, k)
+    assert S.stats()["launches"] == sum(1 for _ in qs)
+    S.close()
+
+
+def test_server_timeout_is_per_query():
+    gs = [synth.rmat(14, 16, seed=6), synth.complete_graph(20), synth.erdos_renyi(2000, 0.01, 0)]
+    S = make_server(gs, max_batch=64, slots=2)
+    S.set_time_limit(0.3)
+    heavy = S.submit(0, 10)  # billions of 9-cliques to enumerate: cannot finish in 0.3 s
+    light = [S.submit(1, 5), S.submit(2, 3), S.submit(1, 20), S.submit(2, 4)]
+    r = wait(S, heavy)
+    assert r["status"] == kclique.KC_E_TIMEOUT
+    for t, (g, k) in zip(light, [(1, 5), (2, 3), (1, 20), (2, 4)]):
+        check(wait(S, t), gs, g, k)
+    S.close()
+
+
+def test_server_budget_and_arguments():
+    lib()
+    with pytest.raises(kclique.KCError):
+        kclique.Server(hbm_budget=1 << 10)
+    S = kclique.Server(hbm_budget=8 << 20, max_batch=16, slots=1)
+    S.add_graph(synth.complete_graph(10))
+    with pytest.raises(kclique.KCError) as e:
+        S.add_graph(synth.rmat(17, 16, seed=1))  # its DAG alone exceeds the budget
+    assert e.value.status == kclique.KC_E_NO_MEMORY
+    with pytest.raises(kclique.KCError):
+        S.submit(5, 3)
+    with pytest.raises(kclique.KCError):
+        S.submit(0, 0)
+    assert wait(S, S.submit(0, 4))["total"] == 210
+    S.close()

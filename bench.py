@@ -400,6 +400,174 @@ def run_ours(a, g, plan, world, rank, local_rank):
         print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# batched and serving workloads (many small graphs; a stream of queries)
+# ----------------------------------------------------------------------------
+def run_batch(a, world, rank, local_rank):
+    """4,096 ego networks of BA(500k, 20), k uniform in 3..8: one captured
+    CUDA graph of persistent launches against one launch per query."""
+    import torch
+
+    from paper_2104_13209_gb300 import build, kclique, workloads
+
+    egos, ks = workloads.ego_batch()
+    build.build()
+    kclique.load()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    nq = len(egos)
+    gid = np.arange(nq)
+    B = kclique.Batch(egos)
+    tune_path = os.path.join(CACHE, f"tune_ego{nq}.json")
+    os.makedirs(CACHE, exist_ok=True)
+    if os.path.exists(tune_path):
+        with open(tune_path) as f:
+            tune = kclique.tune_from_list(json.load(f))
+    else:
+        tune = B.tune(gid, ks, sample=256, stream=stream)
+        with open(tune_path, "w") as f:
+            json.dump(kclique.tune_to_list(tune), f)
+    res = torch.zeros(nq * kclique.RESULT_BYTES, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ex = B.capture(gid, ks, res, tune=tune)
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        stream.synchronize()
+        ms = []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.mean(ms))
+
+    launches0 = kclique.launch_count()
+    with ClockSampler(local_rank) as clk:
+        step_ms = timed(lambda: ex.launch(stream), a.steps, a.warmup)
+    launches = kclique.launch_count() - launches0
+    got = kclique.parse_results(bytes(res.cpu().numpy()), nq)
+    total = sum(r.total for r in got)
+    words = sum(r.words for r in got)
+    assert all(r.status == kclique.KC_OK for r in got)
+
+    def per_query():
+        for i in range(nq):
+            B.count_async(gid[i:i + 1], ks[i:i + 1], res[i * kclique.RESULT_BYTES:(i + 1) * kclique.RESULT_BYTES],
+                          tune=tune, stream=stream)
+
+    plain_ms = timed(per_query, 1, 1)
+    # end to end through the public call from host arrays, results read back
+    e2e = []
+    for _ in range(max(1, a.warmup)):
+        B.count(gid, ks, tune=tune, stream=stream)
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        r2 = B.count(gid, ks, tune=tune, stream=stream)
+        e2e.append(time.perf_counter() - t0)
+    assert [r.total for r in r2] == [r.total for r in got]
+    peak = 2.0 * SMS * POPC_PER_SM_CLK * SM_MAX_HZ / 1e12
+    achieved = 2.0 * words / (step_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": nq / (step_ms / 1e3), "unit": "queries/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"batched: {nq} radius-1 ego networks of BA(500000, m=20), 50-5000 vertices, "
+                               "k uniform in 3..8, degeneracy orientation",
+                   "cliques": str(total), "launch": "one captured CUDA graph of persistent batched launches",
+                   "tune": kclique.tune_to_list(tune), "l2": "flushed between timed steps"},
+        "plain": {"value": nq / (plain_ms / 1e3), "unit": "queries/s", "ms_per_step": plain_ms,
+                  "launch": "one batched launch sequence per query"},
+        "e2e": {"value": nq / float(np.mean(e2e)), "unit": "queries/s", "h2d_bytes_per_step": nq * 56,
+                "d2h_bytes_per_step": nq * kclique.RESULT_BYTES},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_count_batch (whole step)",
+                     "peak_note": "derived: 152 SMs x 16 popc/clk x 2.07 GHz x 2 ops (AND + POPC) per word"},
+        "clocks": clk.summary(), "gpu_launches": launches,
+    }
+    if not a.no_cpu_baseline:
+        from oracle import oracle as O
+
+        t0 = time.perf_counter()
+        done = 0
+        while done < nq and time.perf_counter() - t0 < a.cpu_budget:
+            h = egos[done]
+            O.count(h.row_ptr, h.col_idx, int(ks[done]), threads=O.default_threads())
+            done += 1
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": done / dt, "unit": "queries/s", "cores": O.default_threads(),
+                                "kind": "oracle", "sample": f"the first {done} queries ({dt:.1f} s)"}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(a, world, rank, local_rank):
+    """The 64-graph pool under a Poisson query stream: the continuous-batching
+    server against the same stream served one launch per query."""
+    from paper_2104_13209_gb300 import workloads
+
+    gs = workloads.serve_pool()  # worker processes are spawned before any CUDA use
+    import torch
+
+    from paper_2104_13209_gb300 import build, kclique
+
+    build.build()
+    kclique.load()
+    torch.cuda.set_device(local_rank)
+    ts, gq, kq, pq = workloads.query_stream(a.rate, a.serve_seconds, len(gs))
+    out = {}
+    for mode in a.serve_modes.split(","):
+        S = kclique.Server(hbm_budget=200 << 30, max_batch=256, slots=4, serial=(mode == "plain"))
+        S.set_time_limit(a.time_limit)
+        for h in gs:
+            S.add_graph(h)
+        for i in range(min(64, len(ts))):  # warm-up: every kernel once
+            S.poll(S.submit(int(gq[i]), int(kq[i]), bool(pq[i])), -1)
+        tickets = []
+        t0 = time.perf_counter()
+        for i in range(len(ts)):
+            d = t0 + ts[i] - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets.append(S.submit(int(gq[i]), int(kq[i]), bool(pq[i])))
+        rs = [S.poll(t, -1) for t in tickets]
+        wall = time.perf_counter() - t0
+        lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in rs])
+        span = (max(r["t_done_ms"] for r in rs) - min(r["t_submit_ms"] for r in rs)) / 1e3
+        out[mode] = {"queries": len(rs), "qps": len(rs) / span, "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                     "timeouts": int(sum(r["status"] == kclique.KC_E_TIMEOUT for r in rs)),
+                     "errors": int(sum(r["status"] not in (kclique.KC_OK, kclique.KC_E_TIMEOUT) for r in rs)),
+                     "launches": S.stats()["launches"] - min(64, len(ts)), "wall_s": wall,
+                     "totals": [r["total"] if r["status"] == kclique.KC_OK else None for r in rs]}
+        S.close()
+    modes = list(out)
+    mismatch = 0
+    if len(modes) == 2:
+        for x, y in zip(out[modes[0]]["totals"], out[modes[1]]["totals"]):
+            if x is not None and y is not None and x != y:
+                mismatch += 1
+    main_mode = modes[0]
+    line = {
+        "metric": METRIC, "value": out[main_mode]["qps"], "unit": "queries/s", "n_gpus": world, "steps": 1,
+        "warmup": 1, "ms_per_step": 1e3 * out[main_mode]["wall_s"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"serving: pool of {len(gs)} graphs (16 ER, 24 R-MAT 14-18, 24 Chung-Lu 100k-1M), "
+                               f"Poisson {a.rate:g} req/s for {a.serve_seconds:g} s, k uniform 3..12, pivot p=0.5",
+                   "time_limit_s": a.time_limit, "max_batch": 256, "slots": 4},
+        "latency_ms": {"p50": out[main_mode]["p50_ms"], "p99": out[main_mode]["p99_ms"]},
+        "served": {m: {k: v for k, v in out[m].items() if k != "totals"} for m in modes},
+        "mismatches": mismatch,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -410,6 +578,11 @@ def main():
     ap.add_argument("--scale", type=int, default=20)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "batch", "serve"])
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--time-limit", type=float, default=0.25)
+    ap.add_argument("--serve-modes", default="batched,plain")
     a = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -420,6 +593,12 @@ def main():
 
         backend = "nccl" if torch.cuda.is_available() else "gloo"
         dist.init_process_group(backend=backend)
+    if a.workload == "batch" and a.impl == "ours":
+        run_batch(a, world, rank, local_rank)
+        return
+    if a.workload == "serve" and a.impl == "ours":
+        run_serve(a, world, rank, local_rank)
+        return
     g = workload_graph(a.scale)
     plan = parse_plan(a.plan)
     if a.impl == "reference":

@@ -292,10 +292,11 @@ kc_status kc_batch_exec_destroy(kc_batch_exec* e);
  * answers count queries (graph, k, pivot) from a worker thread of its own:
  * orientation-mode queries that arrive while others run are packed, up to
  * max_batch at a time, into persistent batched launches on `slots` streams
- * that overlap on the device, and each query's result is served as soon as
- * its last root completes.  Pivot-mode queries (Fig. 3, fixed k), and
- * orientation queries whose bitmaps exceed shared memory, run one at a time
- * on the graph's own path.  Counts are those of kc_count / kc_count128. */
+ * that overlap on the device (each on SMs / slots of the GPU), and each
+ * query's result is served as soon as its last root completes.  Pivot-mode
+ * queries (Fig. 3, fixed k), and orientation queries whose bitmaps exceed
+ * shared memory, take a slot each on the graph's own path, one per graph at
+ * a time.  Counts are those of kc_count / kc_count128. */
 typedef struct kc_server kc_server;
 
 typedef struct kc_server_result {
@@ -317,8 +318,8 @@ typedef struct kc_server_result {
 
 /* hbm_budget: device bytes the server may keep resident (slots and graphs);
  * a graph that would exceed it is refused with KC_E_NO_MEMORY.
- * max_batch >= 1 queries per batched launch; slots >= 1 batched launches in
- * flight.  flags: 0 or KC_SERVER_SERIAL.  The calling thread's current
+ * max_batch >= 1 queries per batched launch; slots >= 1 launches in flight.
+ * flags: 0 or KC_SERVER_SERIAL.  The calling thread's current
  * device is the server's. */
 kc_status kc_server_create(size_t hbm_budget, uint32_t max_batch, uint32_t slots, int flags, kc_server** out);
 

@@ -2,18 +2,20 @@
 // graphs and a worker thread that admits count queries as they arrive.
 //
 // Orientation-mode queries (pivot = 0) whose graphs fit the batched kernel
-// wait in one queue; whenever one of the batch slots (a stream with its own
-// working memory) is free, the worker packs up to max_batch of them into one
-// persistent launch (batch_launch), so queries that arrive while others run
-// start on the next free slot and their launches overlap on the device.
-// Each query's result is published to host-mapped memory by the thread that
-// completes its last root, so it is served before the rest of its launch
-// ends.  Persistent launches hold their SMs until done, so every batch slot
-// and the graph path launch on a fixed share of the SMs (SMs / (slots + 1))
-// and a long launch cannot starve the others.  Pivot queries, and orientation queries whose bitmaps need global
-// memory, run one at a time through the graph's own path (kc_count_async).
-// A query is admitted while the server's resident bytes stay within its
-// device-memory budget and the device reports that much memory free.
+// wait in one queue; whenever a slot (a stream with its own working memory)
+// is free, the worker packs up to max_batch of them into one persistent
+// launch (batch_launch), so queries that arrive while others run start on
+// the next free slot and their launches overlap on the device.  Each query's
+// result is published to host-mapped memory by the thread that completes its
+// last root, so it is served before the rest of its launch ends.  Pivot
+// queries, and orientation queries whose bitmaps need global memory, take a
+// slot each and run through the graph's own path (kc_count_async), at most
+// one per graph at a time (they share the graph's working memory).
+// Persistent launches hold their SMs until done, so every slot launches on a
+// fixed share of the SMs (SMs / slots) and a long launch cannot starve the
+// others.  A graph is admitted while the server's resident bytes stay within
+// its device-memory budget, and a graph-path query while the device reports
+// enough free memory for that path's buffers.
 #include <stdio.h>
 #include <string.h>
 
@@ -57,15 +59,8 @@ struct BatchSlot {
     std::vector<uint64_t> tickets;
     std::vector<char> finished;
     bool busy = false;
-};
-
-struct SingleSlot {
-    cudaStream_t st = nullptr;
-    cudaEvent_t ev = nullptr;
-    DevBuf res;
-    kc_result* res_h = nullptr;
-    uint64_t ticket = 0;
-    bool busy = false;
+    bool single = false;          // running one query through its graph's own path
+    uint32_t graph = 0;           // that query's graph
 };
 
 static constexpr uint32_t MAX_GROUPS = 16;
@@ -85,7 +80,7 @@ using namespace kc::srv;
 struct kc_server {
     int device = 0;
     int sms = 0;
-    int share = 0;        // SMs' worth of blocks per launch: every slot's launches fit side by side
+    int share = 0;        // SMs' worth of blocks per launch: every slot's launch fits side by side
     size_t budget = 0;
     size_t resident = 0;
     uint32_t max_batch = 1;
@@ -95,7 +90,7 @@ struct kc_server {
     std::deque<Ticket> tickets;
     std::deque<uint64_t> q_batch, q_single;
     std::vector<BatchSlot> bs;
-    SingleSlot ss;
+    std::vector<char> graph_busy;  // a single-path query of this graph is in flight
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::thread worker;
@@ -226,9 +221,10 @@ void launch_batch(kc_server* S, BatchSlot& b) {
     b.busy = true;  // result slot i <-> b.tickets[i]
 }
 
-void launch_single(kc_server* S) {
-    const uint64_t t = S->q_single.front();
-    S->q_single.pop_front();
+// Run the queued single-path query at position pos of q_single on slot b.
+void launch_single(kc_server* S, BatchSlot& b, size_t pos) {
+    const uint64_t t = S->q_single[pos];
+    S->q_single.erase(S->q_single.begin() + pos);
     Ticket& T = S->tickets[t];
     kc_graph* g = S->graphs[T.graph];
     size_t fr = 0, tot = 0;
@@ -240,78 +236,80 @@ void launch_single(kc_server* S) {
     T.state = 1;
     T.t_admit = S->now_ms();
     T.launch = (uint32_t)++S->launches;
-    kc_status st = kc_count_async(g, T.k, T.pivot, KC_SCHEME_AUTO, 0, (kc_result*)S->ss.res.ptr, nullptr, S->ss.st);
+    kc_status st = kc_count_async(g, T.k, T.pivot, KC_SCHEME_AUTO, 0, (kc_result*)b.res.ptr, nullptr, b.st);
     if (st == KC_OK) {
-        cudaError_t e = cudaMemcpyAsync(S->ss.res_h, S->ss.res.ptr, sizeof(kc_result), cudaMemcpyDeviceToHost, S->ss.st);
-        if (e == cudaSuccess) e = cudaEventRecord(S->ss.ev, S->ss.st);
+        cudaError_t e = cudaMemcpyAsync(b.res_h, b.res.ptr, sizeof(kc_result), cudaMemcpyDeviceToHost, b.st);
+        if (e == cudaSuccess) e = cudaEventRecord(b.ev, b.st);
         if (e != cudaSuccess) st = cuda_error(e, "single result", __FILE__, __LINE__);
     }
     if (st != KC_OK) {
-        cudaStreamSynchronize(S->ss.st);
+        cudaStreamSynchronize(b.st);
         finish(S, t, error_result(st));
         return;
     }
-    S->ss.ticket = t;
-    S->ss.busy = true;
+    b.tickets.assign(1, t);
+    b.finished.assign(1, 0);
+    b.single = true;
+    b.graph = T.graph;
+    S->graph_busy[T.graph] = 1;
+    b.busy = true;
+}
+
+// The first queued single-path query (within a short look-ahead) whose
+// graph has no single-path query in flight, or -1.
+long next_single(kc_server* S) {
+    const size_t look = std::min<size_t>(S->q_single.size(), 64);
+    for (size_t i = 0; i < look; ++i)
+        if (!S->graph_busy[S->tickets[S->q_single[i]].graph]) return (long)i;
+    return -1;
 }
 
 void worker_main(kc_server* S) {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
+    const bool serial = (S->flags & KC_SERVER_SERIAL) != 0;
     while (!S->stop) {
         bool progress = false, busy = false;
         for (BatchSlot& b : S->bs) {
             if (!b.busy) continue;
-            for (size_t i = 0; i < b.tickets.size(); ++i)
-                if (!b.finished[i] && *(volatile unsigned*)&b.done_h[i]) {
-                    kc_result r;
-                    memcpy(&r, (const void*)&b.early_h[i], sizeof(r));
-                    finish(S, b.tickets[i], r);
-                    b.finished[i] = 1;
-                    progress = true;
-                }
+            if (!b.single)
+                for (size_t i = 0; i < b.tickets.size(); ++i)
+                    if (!b.finished[i] && *(volatile unsigned*)&b.done_h[i]) {
+                        kc_result r;
+                        memcpy(&r, (const void*)&b.early_h[i], sizeof(r));
+                        finish(S, b.tickets[i], r);
+                        b.finished[i] = 1;
+                        progress = true;
+                    }
             if (cudaEventQuery(b.ev) == cudaSuccess) {
                 for (size_t i = 0; i < b.tickets.size(); ++i)
                     if (!b.finished[i]) finish(S, b.tickets[i], b.res_h[i]);
+                if (b.single) S->graph_busy[b.graph] = 0;
                 b.busy = false;
-                progress = true;
-            } else {
-                busy = true;
-            }
-        }
-        if (S->ss.busy) {
-            if (cudaEventQuery(S->ss.ev) == cudaSuccess) {
-                finish(S, S->ss.ticket, *S->ss.res_h);
-                S->ss.busy = false;
+                b.single = false;
                 progress = true;
             } else {
                 busy = true;
             }
         }
         if (progress) S->cv_done.notify_all();
-        const bool serial = (S->flags & KC_SERVER_SERIAL) != 0;
-        bool any_busy = S->ss.busy;
-        for (BatchSlot& b : S->bs) any_busy = any_busy || b.busy;
-        if (!(serial && any_busy)) {
-            // one single-path query at a time; in serial mode the oldest query goes first
-            bool single_first = !S->q_single.empty() &&
-                                (S->q_batch.empty() || S->q_single.front() < S->q_batch.front());
-            if (!S->ss.busy && !S->q_single.empty() && (!serial || single_first)) {
-                launch_single(S);
-                progress = true;
-            } else {
-                for (BatchSlot& b : S->bs) {
-                    if (b.busy || S->q_batch.empty()) continue;
-                    if (serial && any_busy) break;
-                    launch_batch(S, b);
-                    progress = true;
-                    any_busy = true;
-                    if (serial) break;
-                }
-            }
+        // admission: every free slot takes the oldest waiting work it can run
+        for (BatchSlot& b : S->bs) {
+            if (b.busy) continue;
+            if (serial && busy) break;
+            const long si = next_single(S);
+            const bool have_single = si >= 0;
+            if (!have_single && S->q_batch.empty()) break;
+            if (have_single && (S->q_batch.empty() || S->q_single[(size_t)si] < S->q_batch.front()))
+                launch_single(S, b, (size_t)si);
+            else
+                launch_batch(S, b);
+            progress = true;
+            busy = busy || b.busy;
+            if (serial) break;
         }
         if (progress) continue;
-        if (busy || S->ss.busy) {
+        if (busy) {
             lk.unlock();
             std::this_thread::sleep_for(std::chrono::microseconds(20));
             lk.lock();
@@ -353,8 +351,8 @@ kc_status kc_server_create(size_t hbm_budget, uint32_t max_batch, uint32_t slots
     cudaGetDevice(&S->device);
     S->sms = sm_count_of_current_device();
     // persistent launches keep their SMs until their work is done, so each
-    // batch slot and the graph path get a fixed share (all of it when serial)
-    S->share = (flags & KC_SERVER_SERIAL) ? S->sms : std::max(1, S->sms / (int)(slots + 1));
+    // slot gets a fixed share (all of it when serial)
+    S->share = (flags & KC_SERVER_SERIAL) ? S->sms : std::max(1, S->sms / (int)slots);
     auto fail = [&](kc_status st) {
         kc_server_destroy(S);
         return st;
@@ -374,16 +372,11 @@ kc_status kc_server_create(size_t hbm_budget, uint32_t max_batch, uint32_t slots
         if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&b.done_d, b.done_h, 0);
         if (e != cudaSuccess) return fail(cuda_error(e, "batch slot", __FILE__, __LINE__));
         kc_status st = dev_alloc(b.ws, batch_slot_bytes(S->max_batch));
+        if (st == KC_OK && b.res_h == nullptr) st = set_error(KC_E_NO_MEMORY, "host allocation failed");
         if (st == KC_OK) st = dev_alloc(b.res, (size_t)S->max_batch * sizeof(kc_result));
         if (st != KC_OK) return fail(st);
         S->resident += b.ws.bytes + b.res.bytes;
     }
-    e = cudaStreamCreateWithFlags(&S->ss.st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ss.ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaHostAlloc((void**)&S->ss.res_h, sizeof(kc_result), 0);
-    if (e != cudaSuccess) return fail(cuda_error(e, "single slot", __FILE__, __LINE__));
-    kc_status st = dev_alloc(S->ss.res, sizeof(kc_result) + 64);
-    if (st != KC_OK) return fail(st);
     if (S->resident > S->budget)
         return fail(set_error(KC_E_NO_MEMORY, "the slots alone (%zu bytes) exceed the budget", S->resident));
     S->worker = std::thread(worker_main, S);
@@ -412,6 +405,7 @@ kc_status kc_server_add_graph(kc_server* S, const uint32_t* row_ptr, const uint3
     S->resident += info.device_bytes;
     *graph_id = (uint32_t)S->graphs.size();
     S->graphs.push_back(g);
+    S->graph_busy.push_back(0);
     return KC_OK;
 }
 
@@ -492,11 +486,6 @@ kc_status kc_server_destroy(kc_server* S) {
     S->cv_work.notify_all();
     if (S->worker.joinable()) S->worker.join();
     for (BatchSlot& b : S->bs) free_slot(b);
-    if (S->ss.st) cudaStreamSynchronize(S->ss.st);
-    if (S->ss.ev) cudaEventDestroy(S->ss.ev);
-    if (S->ss.st) cudaStreamDestroy(S->ss.st);
-    dev_free(S->ss.res);
-    if (S->ss.res_h) cudaFreeHost(S->ss.res_h);
     for (kc_graph* g : S->graphs) kc_graph_destroy(g);
     if (S->setup) cudaStreamDestroy(S->setup);
     delete S;

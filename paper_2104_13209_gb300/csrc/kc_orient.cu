@@ -100,11 +100,17 @@ __global__ void k_degree_key(const uint32_t* __restrict__ rp, uint32_t n, uint32
 // orientation key is its sub-round index; its core number is L.  A vertex
 // removed at level L had at most L remaining neighbours, so the DAG that
 // orients edges by (round, id) has out-degree <= degeneracy.
+// Each level's scan reads only the vertices still remaining and writes the
+// survivors to the other list, and a vertex is marked removed when it
+// enters a frontier (two grid barriers per sub-round).  Decrements from its
+// own entry round still reach it, so its final degree is its remaining
+// degree at removal (the second orientation key, k_removal_degree).
 // ---------------------------------------------------------------------------
 struct PeelCtl {
     unsigned fcount[2];
+    unsigned rcount[2];     // lengths of the remaining-vertex lists being built
     unsigned minrem[2];
-    unsigned heavy_count;
+    unsigned hcount[2];     // heavy-list length, by round parity
     unsigned bar_count;
     unsigned bar_gen;
     unsigned flags;
@@ -173,16 +179,26 @@ __device__ __forceinline__ unsigned block_read(unsigned* p) {
 
 // deg[] and round_of[] change under other SMs between grid barriers: read
 // them from L2 (ld.global.cg) so no stale L1 line is ever used.
+// A neighbour w of a vertex removed in round `round` loses one degree unless
+// it was removed before (round_of[w] <= round).  The decrement that brings
+// it to `level` pushes it into the next frontier and marks it removed in
+// round + 1 at once; decrements by other vertices of this round still
+// reach it, so that its final degree is its remaining degree at removal.
 __device__ __forceinline__ void peel_neighbour(const uint32_t* ci, uint32_t j, bool in_range, uint32_t level,
-                                               int* deg, const uint32_t* round_of, uint32_t* Fn, unsigned* fcn,
-                                               uint32_t n, unsigned* flags) {
+                                               uint32_t round, int* deg, uint32_t* round_of, uint32_t* core,
+                                               uint32_t* Fn, unsigned* fcn, uint32_t n, unsigned* flags) {
     bool push = false;
     uint32_t w = 0;
     if (in_range) {
         w = ci[j];
-        if (w < n && __ldcg(&round_of[w]) == UNSET) {
+        const uint32_t r = w < n ? __ldcg(&round_of[w]) : 0u;
+        if (w < n && (r == UNSET || r == round + 1)) {
             int old = atomicSub(&deg[w], 1);
             push = (old == (int)level + 1);
+            if (push) {
+                __stcg(&round_of[w], round + 1);
+                core[w] = level;
+            }
         }
     }
     warp_push(push, w, Fn, fcn, n, flags);
@@ -199,37 +215,63 @@ __device__ __forceinline__ bool peel_barrier(PeelCtl* c, uint32_t nb, uint32_t& 
 __global__ void __launch_bounds__(256) k_peel(const uint32_t* __restrict__ rp, const uint32_t* __restrict__ ci,
                                               uint32_t n, int* deg, uint32_t* round_of, uint32_t* core, uint32_t* F0,
                                               uint32_t* F1, uint32_t* heavy, PeelCtl* c, unsigned long long* nf_log,
-                                              uint32_t* atrem) {
+                                              uint32_t* R0, uint32_t* R1) {
     const uint32_t nb = gridDim.x;
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t gthreads = gridDim.x * blockDim.x;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = gtid >> 5, nwarps = gthreads >> 5;
     uint32_t* F[2] = {F0, F1};
+    uint32_t* R[2] = {R0, R1};  // remaining vertices: each scan reads one list and writes the next
     uint32_t level = 0, round = 0, remaining = n;
     int cur = 0;
+    int rc = 0;                 // the list the next scan reads (the first scan reads every vertex)
+    uint32_t rn = n;            // its length
+    bool all = true;
     uint32_t it = 0;
     uint32_t seq = 0;
     while (remaining > 0) {
-        // scan: collect remaining vertices with degree <= level; track the
-        // smallest degree above it
+        // scan: collect remaining vertices with degree <= level, keep the
+        // others in the next remaining list, and track the smallest degree
+        // above the level
         unsigned* mr = &c->minrem[it & 1];
+        const int rx = rc ^ 1;
         uint32_t local_min = UNSET;
-        for (uint32_t base = gwarp * 32; base < n; base += nwarps * 32) {
-            uint32_t v = base + lane;
-            bool take = false;
-            if (v < n && __ldcg(&round_of[v]) == UNSET) {
-                int d = __ldcg(&deg[v]);
-                if (d <= (int)level) take = true;
-                else local_min = min(local_min, (uint32_t)d);
+        for (uint32_t base = gwarp * 32; base < rn; base += nwarps * 32) {
+            const uint32_t idx = base + lane;
+            uint32_t v = 0;
+            bool take = false, keep = false;
+            if (idx < rn) {
+                v = all ? idx : __ldcg(&R[rc][idx]);
+                if (__ldcg(&round_of[v]) == UNSET) {
+                    int d = __ldcg(&deg[v]);
+                    if (d <= (int)level) {
+                        take = true;
+                        __stcg(&round_of[v], round);  // removed in this level's first round
+                        core[v] = level;
+                    } else {
+                        keep = true;
+                        local_min = min(local_min, (uint32_t)d);
+                    }
+                }
             }
             warp_push(take, v, F[cur], &c->fcount[cur], n, &c->flags);
+            warp_push(keep, v, R[rx], &c->rcount[rx], n, &c->flags);
         }
         for (int o = 16; o > 0; o >>= 1) local_min = min(local_min, __shfl_xor_sync(0xffffffffu, local_min, o));
         if (lane == 0 && local_min != UNSET) atomicMin(mr, local_min);
         if (!peel_barrier(c, nb, seq)) return;
         if (gtid == 0) atomicExch(&c->minrem[(it + 1) & 1], UNSET);
         ++it;
+        {
+            // the list just written is the next one to read; the counter of the
+            // one just read is free (every block read it before this barrier)
+            const uint32_t rn_new = block_read(&c->rcount[rx]);
+            if (gtid == 0) atomicExch(&c->rcount[rc], 0u);
+            rc = rx;
+            rn = min(rn_new, n);
+            all = false;
+        }
         uint32_t nf = block_read(&c->fcount[cur]);
         log_nf(c, nf_log, nf, seq);
         if (nf > n || (block_read(&c->flags) & KC_FLAG_INTERNAL)) return;  // recorded in flags
@@ -244,52 +286,49 @@ __global__ void __launch_bounds__(256) k_peel(const uint32_t* __restrict__ rp, c
             continue;
         }
         while (nf > 0) {
+            // the frontier F[cur] is already marked removed in `round`
             const int nxt = cur ^ 1;
-            for (uint32_t i = gtid; i < nf; i += gthreads) {
-                uint32_t v = __ldcg(&F[cur][i]);
-                __stcg(&round_of[v], round);
-                core[v] = level;
-                atrem[v] = (uint32_t)max(0, __ldcg(&deg[v]));  // remaining degree when removed
-            }
             if (gtid == 0) atomicMax(&c->max_level, level);
-            if (!peel_barrier(c, nb, seq)) return;
+            // Counter resets sit between two grid barriers and the next use of
+            // the counter: the other parity's heavy counter (last read in the
+            // previous round's heavy phase, next written in the next round's
+            // light phase) is cleared here, and this frontier's counter in the
+            // heavy phase below.
+            if (gtid == 0) atomicExch(&c->hcount[(round + 1) & 1], 0u);
             // light frontier vertices: one warp each
             for (uint32_t i = gwarp; i < nf; i += nwarps) {
                 uint32_t u = __ldcg(&F[cur][i]);
                 uint32_t b = rp[u], e = rp[u + 1];
                 if (e - b > HEAVY_DEG) {
                     if (lane == 0) {
-                        uint32_t hpos = atomicAdd(&c->heavy_count, 1u);
+                        uint32_t hpos = atomicAdd(&c->hcount[round & 1], 1u);
                         if (hpos < n) __stcg(&heavy[hpos], u);
                         else atomicOr(&c->flags, (unsigned)KC_FLAG_INTERNAL);
                     }
                     continue;
                 }
                 for (uint32_t j0 = b; j0 < e; j0 += 32)
-                    peel_neighbour(ci, j0 + lane, j0 + lane < e, level, deg, round_of, F[nxt], &c->fcount[nxt], n,
-                                   &c->flags);
+                    peel_neighbour(ci, j0 + lane, j0 + lane < e, level, round, deg, round_of, core, F[nxt],
+                                   &c->fcount[nxt], n, &c->flags);
             }
             if (!peel_barrier(c, nb, seq)) return;
-            // heavy frontier vertices: the whole grid on each
-            uint32_t hc = min(block_read(&c->heavy_count), n);
+            // heavy frontier vertices: the whole grid on each.  Every block
+            // read nf before the light barrier: this frontier's counter is free.
+            if (gtid == 0) atomicExch(&c->fcount[cur], 0u);
+            uint32_t hc = min(block_read(&c->hcount[round & 1]), n);
             for (uint32_t h = 0; h < hc; ++h) {
                 uint32_t u = __ldcg(&heavy[h]);
                 uint32_t b = rp[u], e = rp[u + 1];
                 for (uint32_t j0 = b + gwarp * 32; j0 < e; j0 += nwarps * 32)
-                    peel_neighbour(ci, j0 + lane, j0 + lane < e, level, deg, round_of, F[nxt], &c->fcount[nxt], n,
-                                   &c->flags);
+                    peel_neighbour(ci, j0 + lane, j0 + lane < e, level, round, deg, round_of, core, F[nxt],
+                                   &c->fcount[nxt], n, &c->flags);
             }
             if (!peel_barrier(c, nb, seq)) return;
             remaining -= nf;
             ++round;
-            // every block read fcount[cur] and heavy_count before the last barrier
             uint32_t nf_next = block_read(&c->fcount[nxt]);
             log_nf(c, nf_log, nf_next, seq);
             if (nf_next > n || (block_read(&c->flags) & KC_FLAG_INTERNAL)) return;  // recorded in flags
-            if (gtid == 0) {
-                atomicExch(&c->fcount[cur], 0u);
-                atomicExch(&c->heavy_count, 0u);
-            }
             cur = nxt;
             nf = nf_next;
         }
@@ -304,6 +343,12 @@ __global__ void __launch_bounds__(256) k_peel(const uint32_t* __restrict__ rp, c
 // ---------------------------------------------------------------------------
 // Relabel + filter
 // ---------------------------------------------------------------------------
+// remaining degree of every vertex when it was removed (its final degree)
+__global__ void k_removal_degree(const int* __restrict__ deg, uint32_t n, uint32_t* __restrict__ atrem) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) atrem[v] = (uint32_t)max(0, deg[v]);
+}
+
 __global__ void k_invert(const uint32_t* __restrict__ old_of_new, uint32_t n, uint32_t* __restrict__ new_of_old) {
     uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) new_of_old[old_of_new[r]] = r;
@@ -454,7 +499,7 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
     // scratch: small control words + per-vertex arrays
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     DevBuf work;
-    size_t wbytes = al(sizeof(PeelCtl)) + al(64) + 6 * al((size_t)n * 4 + 4) + al(((size_t)nnz / 2 + 1) * 4) +
+    size_t wbytes = al(sizeof(PeelCtl)) + al(64) + 8 * al((size_t)n * 4 + 4) + al(((size_t)nnz / 2 + 1) * 4) +
                     al((size_t)NF_LOG * 8);
     kc_status st = dev_alloc(work, wbytes);
     if (st != KC_OK) return st;
@@ -467,6 +512,8 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
     uint32_t* F0 = (uint32_t*)p; p += al((size_t)n * 4 + 4);
     uint32_t* F1 = (uint32_t*)p; p += al((size_t)n * 4 + 4);
     uint32_t* heavy = (uint32_t*)p; p += al((size_t)n * 4 + 4);
+    uint32_t* R0 = (uint32_t*)p; p += al((size_t)n * 4 + 4);
+    uint32_t* R1 = (uint32_t*)p; p += al((size_t)n * 4 + 4);
     uint32_t* colbuf = (uint32_t*)p; p += al(((size_t)nnz / 2 + 1) * 4);
     unsigned long long* nf_log = (unsigned long long*)p;
 
@@ -538,7 +585,7 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
             KC_TRY(cudaMemsetAsync(nf_log, 0xFF, (size_t)NF_LOG * 8, s));
             void* args[] = {(void*)&a_rp, (void*)&a_ci, (void*)&a_n, (void*)&deg, (void*)&round_of,
                             (void*)&a_core, (void*)&F0, (void*)&F1, (void*)&heavy, (void*)&ctl, (void*)&nf_log,
-                            (void*)&key};
+                            (void*)&R0, (void*)&R1};
             KC_TRY(cudaLaunchCooperativeKernel((const void*)k_peel, dim3(blocks), dim3(256), args, 0, s));
             note_launch();
             PeelCtl hc;
@@ -560,6 +607,9 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
                                       hc.mismatch[4], hc.rounds, hc.max_level));
             g->degeneracy = hc.max_level;
             max_key = hc.rounds;
+            k_removal_degree<<<grid_for(n, 256, sms), 256, 0, s>>>(deg, n, key);
+            note_launch();
+            KC_TRY(cudaGetLastError());
         } else {
             g->degeneracy = 0;
         }

@@ -15,7 +15,10 @@
 // fixed share of the SMs (SMs / slots) and a long launch cannot starve the
 // others.  A graph is admitted while the server's resident bytes stay within
 // its device-memory budget, and a graph-path query while the device reports
-// enough free memory for that path's buffers.
+// enough free memory for that path's buffers.  Waiting queries are admitted
+// cheapest first (by a size estimate), except that a query waiting longer
+// than a second goes before any cheaper one; the serial baseline keeps
+// arrival order.
 #include <stdio.h>
 #include <string.h>
 
@@ -134,11 +137,48 @@ kc_result error_result(kc_status st) {
     return r;
 }
 
+// Estimated cost of a queued query (cheapest first within admission).
+double cost_of(const kc_server* S, uint64_t t) {
+    const Ticket& T = S->tickets[t];
+    const kc_graph* g = S->graphs[T.graph];
+    return query_cost_estimate(g->m, g->d_max, T.k);
+}
+
+// Queries that waited this long are admitted before cheaper ones.
+static constexpr double AGE_LIMIT_MS = 1000.0;
+
+// Move the n cheapest queries of q (any that waited beyond AGE_LIMIT_MS
+// first, oldest first) into out, in queue order.
+void take_cheapest(kc_server* S, std::deque<uint64_t>& q, uint32_t n, std::vector<uint64_t>& out) {
+    out.clear();
+    if (S->flags & KC_SERVER_SERIAL) {  // the plain baseline keeps arrival order
+        out.assign(q.begin(), q.begin() + std::min<size_t>(n, q.size()));
+        q.erase(q.begin(), q.begin() + out.size());
+        return;
+    }
+    if (n >= q.size()) {
+        out.assign(q.begin(), q.end());
+        q.clear();
+        return;
+    }
+    const double now = S->now_ms();
+    std::vector<std::pair<double, size_t>> key(q.size());
+    for (size_t i = 0; i < q.size(); ++i) {
+        const bool old = now - S->tickets[q[i]].t_submit > AGE_LIMIT_MS;
+        key[i] = {old ? -1.0 - (double)(q.size() - i) : cost_of(S, q[i]), i};
+    }
+    std::nth_element(key.begin(), key.begin() + n, key.end());
+    std::vector<char> pick(q.size(), 0);
+    for (uint32_t j = 0; j < n; ++j) pick[key[j].second] = 1;
+    std::deque<uint64_t> rest;
+    for (size_t i = 0; i < q.size(); ++i) (pick[i] ? out.push_back(q[i]) : rest.push_back(q[i]));
+    q.swap(rest);
+}
+
 // Pack up to max_batch queued orientation queries into one launch on slot b.
 void launch_batch(kc_server* S, BatchSlot& b) {
     const uint32_t n = (uint32_t)std::min<size_t>(S->q_batch.size(), S->max_batch);
-    b.tickets.assign(S->q_batch.begin(), S->q_batch.begin() + n);
-    S->q_batch.erase(S->q_batch.begin(), S->q_batch.begin() + n);
+    take_cheapest(S, S->q_batch, n, b.tickets);
     b.finished.assign(n, 0);
     // descriptors grouped by configuration
     struct Item {
@@ -258,10 +298,22 @@ void launch_single(kc_server* S, BatchSlot& b, size_t pos) {
 // The first queued single-path query (within a short look-ahead) whose
 // graph has no single-path query in flight, or -1.
 long next_single(kc_server* S) {
-    const size_t look = std::min<size_t>(S->q_single.size(), 64);
-    for (size_t i = 0; i < look; ++i)
-        if (!S->graph_busy[S->tickets[S->q_single[i]].graph]) return (long)i;
-    return -1;
+    if (S->flags & KC_SERVER_SERIAL) return S->q_single.empty() ? -1 : 0;
+    const size_t look = std::min<size_t>(S->q_single.size(), 1024);
+    const double now = S->now_ms();
+    long best = -1;
+    double best_cost = 0;
+    for (size_t i = 0; i < look; ++i) {
+        const uint64_t t = S->q_single[i];
+        if (S->graph_busy[S->tickets[t].graph]) continue;
+        if (now - S->tickets[t].t_submit > AGE_LIMIT_MS) return (long)i;  // waited too long: oldest first
+        const double c = cost_of(S, t);
+        if (best < 0 || c < best_cost) {
+            best = (long)i;
+            best_cost = c;
+        }
+    }
+    return best;
 }
 
 void worker_main(kc_server* S) {
@@ -300,7 +352,8 @@ void worker_main(kc_server* S) {
             const long si = next_single(S);
             const bool have_single = si >= 0;
             if (!have_single && S->q_batch.empty()) break;
-            if (have_single && (S->q_batch.empty() || S->q_single[(size_t)si] < S->q_batch.front()))
+            if (have_single && (S->q_batch.empty() || S->q_single[(size_t)si] < S->q_batch.front() ||
+                                (!serial && cost_of(S, S->q_single[(size_t)si]) <= cost_of(S, S->q_batch.front()))))
                 launch_single(S, b, (size_t)si);
             else
                 launch_batch(S, b);

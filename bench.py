@@ -177,8 +177,9 @@ def run_reference(a, g, plan, world, rank):
         "unit": "cliques/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": 1e3 * secs / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": g.name, "n": g.n, "edges": g.num_edges, "k": k, "orientation": "degeneracy",
-                   "traversal": "graph orientation (Fig. 2), CPU oracle"},
+        "config": {"workload": g.name, "n": g.n, "edges": g.num_edges, "orientation": "degeneracy",
+                   "plan": [f"k={kk} {sch}" for kk, sch in plan],
+                   "traversal": f"graph orientation (Fig. 2), CPU oracle, k = {k} (both splits count the same)"},
         "cpu_baseline": {"value": value, "unit": "cliques/s", "cores": info["threads"], "kind": "oracle",
                          "sample": f"every {info['stride']}-th root with out-degree >= {k - 1} "
                                    f"({info['roots']} roots), orientation {orient_s:.1f}s untimed"},

@@ -153,7 +153,10 @@ kc_status kc_graph_export(const kc_graph* g, uint32_t* dag_row_ptr, uint32_t* da
  *     else 1, 2, 4, 8, 16 or 32 (Section 3.5).
  *   total_out (host): the count modulo 2^64.
  *   per_vertex_out (nullable, n entries, host or device memory): c_k(v), the
- *     number of k-cliques containing input vertex v, modulo 2^64.
+ *     number of k-cliques containing input vertex v, modulo 2^64.  These
+ *     always come from the pivoting traversal restricted to size k, and so
+ *     does the total of such a call, whatever `pivot` says (the counts are
+ *     the same).
  *   flags_out (nullable, host): KC_FLAG_* bits.
  * Returns KC_E_OVERFLOW (with every output written) when the total or a
  * per-vertex count exceeded 2^64 - 1. */
@@ -169,7 +172,8 @@ kc_status kc_count128(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_t s
  * written to result_dev (device memory) when the stream reaches it.  Device
  * working memory is taken from the handle; call kc_graph_reserve first if the
  * call will be captured into a CUDA graph (no allocation happens then).
- * per_vertex_dev: nullable, n entries of device memory, input numbering. */
+ * per_vertex_dev: nullable, n entries of device memory, input numbering
+ * (computed by the pivoting traversal, as in kc_count). */
 kc_status kc_count_async(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_t subwarp, kc_result* result_dev,
                          uint64_t* per_vertex_dev, void* stream);
 

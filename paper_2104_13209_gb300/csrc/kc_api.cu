@@ -245,9 +245,9 @@ kc_status kc_count_async(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_
     if (!result_dev) return set_error(KC_E_INVALID_ARG, "result_dev is NULL");
     if (per_vertex_dev && !is_device_pointer(per_vertex_dev))
         return set_error(KC_E_INVALID_ARG, "per_vertex_dev must be device memory");
-    if (pivot) return count_pivot_async(g, k, result_dev, per_vertex_dev, (cudaStream_t)stream);
-    if (per_vertex_dev)
-        return set_error(KC_E_UNSUPPORTED, "per-vertex counts come from the pivoting traversal (pivot = 1)");
+    // per-vertex counts always come from the pivoting traversal restricted
+    // to size k (the same exact counts)
+    if (pivot || per_vertex_dev) return count_pivot_async(g, k, result_dev, per_vertex_dev, (cudaStream_t)stream);
     return count_launch(g, a, result_dev, (cudaStream_t)stream);
 }
 
@@ -262,8 +262,9 @@ static kc_status count_sync(kc_graph* g, uint32_t k, int pivot, int scheme, uint
     if (!lo_out) return set_error(KC_E_INVALID_ARG, "total_out is NULL");
     CountArgs a;
     KC_CHECK(resolve(g, k, pivot, scheme, subwarp, a));
-    if (per_vertex_out && !pivot)
-        return set_error(KC_E_UNSUPPORTED, "per-vertex counts come from the pivoting traversal (pivot = 1)");
+    // per-vertex counts always come from the pivoting traversal restricted
+    // to size k (the same exact counts)
+    if (per_vertex_out) pivot = 1;
     cudaStream_t s = (cudaStream_t)stream;
     KC_CHECK(dev_alloc(g->result, sizeof(kc_result) + 64));
     kc_result* rd = (kc_result*)g->result.ptr;

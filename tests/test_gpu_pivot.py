@@ -112,3 +112,14 @@ def test_pivot_matches_orientation_traversal():
     counts, ovf, om, _ = G.count_all()
     for k in range(3, min(om, 6) + 1):
         assert int(counts[k]) == G.count(k, scheme="vc").total == G.count(k, scheme="ec").total
+
+
+def test_per_vertex_requested_in_orientation_mode():
+    # per-vertex counts with pivot = 0 are served by the pivoting traversal
+    g = synth.rmat(11, 16, seed=3)
+    drp, dci, _, _ = O.dag_for(g.row_ptr, g.col_idx, "degeneracy")
+    G = graph(g)
+    for k in (3, 5):
+        want = O.count_orient(drp, dci, k, per_vertex=True)
+        tot, pv, fl = G.count_per_vertex(k, pivot=False)
+        assert tot == want.total and [int(x) for x in pv] == want.per_vertex

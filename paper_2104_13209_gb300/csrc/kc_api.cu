@@ -73,8 +73,8 @@ static bool is_device_pointer(const void* p) {
 }  // namespace kc
 
 uint64_t kc_graph::device_bytes() const {
-    const kc::DevBuf* bufs[] = {&row_ptr, &col, &new_of_old, &old_of_new, &core, &roots, &edge_src,
-                                &edge_order, &ctl, &result, &pivot_out, &pv_stage, &scratch, &pv, &tmp};
+    const kc::DevBuf* bufs[] = {&row_ptr, &col, &new_of_old, &old_of_new, &core, &roots, &ctl,
+                                &result, &pivot_out, &pv_stage, &scratch, &pv, &tmp};
     uint64_t t = 0;
     for (auto* b : bufs) t += b->bytes;
     return t;
@@ -165,8 +165,8 @@ kc_status kc_graph_create(const uint32_t* row_ptr, const uint32_t* col_idx, uint
 
 kc_status kc_graph_destroy(kc_graph* g) {
     if (!g) return KC_OK;
-    DevBuf* bufs[] = {&g->row_ptr, &g->col, &g->new_of_old, &g->old_of_new, &g->core, &g->roots, &g->edge_src,
-                      &g->edge_order, &g->ctl, &g->result, &g->pivot_out, &g->pv_stage, &g->scratch, &g->pv, &g->tmp};
+    DevBuf* bufs[] = {&g->row_ptr, &g->col, &g->new_of_old, &g->old_of_new, &g->core, &g->roots, &g->ctl,
+                       &g->result, &g->pivot_out, &g->pv_stage, &g->scratch, &g->pv, &g->tmp};
     for (auto* b : bufs) dev_free(*b);
     delete g;
     return KC_OK;

@@ -84,8 +84,6 @@ struct kc_graph {
     kc::DevBuf old_of_new;   // u32[n]
     kc::DevBuf core;         // u32[n] (input numbering), degeneracy only
     kc::DevBuf roots;        // u32[n] library ids sorted by out-degree, descending
-    kc::DevBuf edge_src;     // u32[m] source of every DAG edge (EC roots), built on first use
-    kc::DevBuf edge_order;   // u32[m] DAG edge ids in work order (EC)
     std::vector<uint64_t> outdeg_hist;  // host: number of vertices per out-degree (d_max + 1 entries)
     // working memory for counting
     kc::DevBuf ctl;          // kc::Ctl + kernel work counters (sized by kc::ctl_bytes())
@@ -118,7 +116,6 @@ kc_status sort_ids_by_key(const uint32_t* key, uint32_t n, uint32_t max_key, uin
 
 // kc_orient.cu
 kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, int validate, cudaStream_t s);
-kc_status ensure_edge_src(kc_graph* g, cudaStream_t s);
 
 // kc_count.cu
 struct CountArgs {

@@ -450,32 +450,6 @@ __global__ void __launch_bounds__(ROWSORT_WARPS * 32) k_sort_rows(const uint32_t
     }
 }
 
-__global__ void k_edge_src(const uint32_t* __restrict__ rp, uint32_t n, uint32_t* __restrict__ src) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t r = gw; r < n; r += nw)
-        for (uint32_t e = rp[r] + lane; e < rp[r + 1]; e += 32) src[e] = r;
-}
-
-// Edge work order: the edges of the roots in root order.
-__global__ void k_root_outdeg(const uint32_t* __restrict__ rp, const uint32_t* __restrict__ roots, uint32_t n,
-                              uint32_t* __restrict__ d) {
-    uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        uint32_t r = roots[i];
-        d[i] = rp[r + 1] - rp[r];
-    }
-}
-
-__global__ void k_edge_order(const uint32_t* __restrict__ rp, const uint32_t* __restrict__ roots,
-                             const uint32_t* __restrict__ off, uint32_t n, uint32_t* __restrict__ order) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t i = gw; i < n; i += nw) {
-        uint32_t r = roots[i], b = rp[r], len = rp[r + 1] - b, o = off[i];
-        for (uint32_t j = lane; j < len; j += 32) order[o + j] = b + j;
-    }
-}
 
 // ---------------------------------------------------------------------------
 
@@ -697,31 +671,5 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
     return KC_OK;
 }
 
-kc_status ensure_edge_src(kc_graph* g, cudaStream_t s) {
-    if (g->edge_src.ptr) return KC_OK;
-    const uint32_t n = g->n;
-    const int sms = g->sm_count;
-    KC_CHECK(dev_alloc(g->edge_src, (size_t)g->m * 4 + 4));
-    KC_CHECK(dev_alloc(g->edge_order, (size_t)g->m * 4 + 4));
-    DevBuf t;
-    KC_CHECK(dev_alloc(t, ((size_t)n + 1) * 8 + 256));
-    uint32_t* d = (uint32_t*)t.ptr;
-    uint32_t* off = d + n + 1;
-    k_edge_src<<<grid_for((uint64_t)n * 32, 256, sms), 256, 0, s>>>((uint32_t*)g->row_ptr.ptr, n,
-                                                                     (uint32_t*)g->edge_src.ptr);
-    note_launch();
-    k_root_outdeg<<<grid_for(n, 256, sms), 256, 0, s>>>((uint32_t*)g->row_ptr.ptr, (uint32_t*)g->roots.ptr, n, d);
-    note_launch();
-    kc_status st = scan_u32(d, off, n, g->tmp, s);
-    if (st == KC_OK) {
-        k_edge_order<<<grid_for((uint64_t)n * 32, 256, sms), 256, 0, s>>>(
-            (uint32_t*)g->row_ptr.ptr, (uint32_t*)g->roots.ptr, off, n, (uint32_t*)g->edge_order.ptr);
-        note_launch();
-        cudaError_t e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) st = cuda_error(e, "edge order", __FILE__, __LINE__);
-    }
-    dev_free(t);
-    return st;
-}
 
 }  // namespace kc

@@ -113,3 +113,17 @@ def test_rmat20_full_size_k4():
         for scheme in ("vc", "ec"):
             assert G.count(4, scheme=scheme).total == rec["counts"]["4"], (orient, scheme)
         G.close()
+
+
+def test_time_limit_returns_timeout_and_keeps_the_handle():
+    # billions of 9-cliques: cannot finish in 50 ms; the wait ends with a
+    # status, the context and the handle stay usable
+    g = synth.rmat(14, 16, seed=6)
+    G = graph(g)
+    G.set_time_limit(0.05)
+    with pytest.raises(kclique.KCError) as e:
+        G.count(10, scheme="ec")
+    assert e.value.status == kclique.KC_E_TIMEOUT
+    G.set_time_limit(0)
+    drp, dci, _, _ = O.dag_for(g.row_ptr, g.col_idx, "degeneracy")
+    assert G.count(3).total == O.count_orient(drp, dci, 3).total

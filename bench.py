@@ -51,6 +51,25 @@ def workload_graph(scale=20, ef=16, seed=0):
     return g
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest x over the ranks of the default process group (x itself
+    when there is one rank): the slowest replica sets the time."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job throughput of `world` replicas that each process
+    units_per_rank units: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def parse_plan(s: str):
     """'4vc,7pv' -> [(4, 'vc'), ...]."""
     out = []
@@ -298,10 +317,7 @@ def run_ours(a, g, plan, world, rank, local_rank):
     for lab, ms in timings:
         per_label[lab] = per_label.get(lab, 0.0) + ms / a.steps
     total_cliques = sum(r.total for r in res)
-    if world > 1:
-        t = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(step_ms, dev)
 
     # end to end through the public API from pinned host memory
     rp_h = torch.from_numpy(g.row_ptr.view(np.int32)).pin_memory()
@@ -327,11 +343,7 @@ def run_ours(a, g, plan, world, rank, local_rank):
         tot = e2e_step()
         e2e_times.append(time.perf_counter() - t0)
         assert tot == total_cliques, "end-to-end count differs from the device-resident count"
-    e2e_s = float(np.mean(e2e_times))
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(float(np.mean(e2e_times)), dev)
 
     # roofline of the dominant kernel (the first count of the plan): the
     # slower of its algorithmic CSR bytes at HBM bandwidth and its AND + POPC
@@ -364,7 +376,7 @@ def run_ours(a, g, plan, world, rank, local_rank):
                  else "derived from unit counts and clock"})
 
     clocks = clk.summary()
-    value = world * total_cliques / (step_ms / 1e3)
+    value = replica_throughput(total_cliques, step_ms / 1e3, world)
     line = {
         "metric": METRIC,
         "value": value,
@@ -385,7 +397,7 @@ def run_ours(a, g, plan, world, rank, local_rank):
             "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
             "wall_s_timed_region": t_wall, "parallelism": f"replicas x{world}",
         },
-        "e2e": {"value": world * total_cliques / e2e_s, "unit": "cliques/s",
+        "e2e": {"value": replica_throughput(total_cliques, e2e_s, world), "unit": "cliques/s",
                 "h2d_bytes_per_step": 4 * (n + 1) + 4 * nnz,
                 "d2h_bytes_per_step": kclique.RESULT_BYTES * len(plan)},
         "roofline": roof,

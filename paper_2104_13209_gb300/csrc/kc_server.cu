@@ -446,8 +446,6 @@ kc_status kc_server_add_graph(kc_server* S, const uint32_t* row_ptr, const uint3
     kc_graph_info info;
     kc_graph_info_get(g, &info);
     std::lock_guard<std::mutex> lk(S->mu);
-    size_t fr = 0, tot = 0;
-    cudaMemGetInfo(&fr, &tot);
     if (S->resident + info.device_bytes > S->budget) {
         kc_graph_destroy(g);
         return set_error(KC_E_NO_MEMORY, "graph of %llu bytes exceeds the server budget",

@@ -245,15 +245,14 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* 
                 while (atomicAdd(gen, 0u) == g) {
                     __nanosleep(64);
                     if ((++spins & 255u) == 0 && globaltimer_ns() - t0 > limit_ns) {
-                        if (atomicOr(flags, (unsigned)KC_FLAG_TIMEOUT) == 0u || true) {
-                            if (dbg && atomicCAS(&dbg[0], 0u, 1u) == 0u) {
-                                dbg[1] = blockIdx.x;
-                                dbg[2] = seq;
-                                dbg[3] = atomicAdd(count, 0u);
-                                dbg[4] = atomicAdd(gen, 0u);
-                                dbg[5] = g;
-                                dbg[6] = (unsigned)(globaltimer_ns() - t0);
-                            }
+                        atomicOr(flags, (unsigned)KC_FLAG_TIMEOUT);
+                        if (dbg && atomicCAS(&dbg[0], 0u, 1u) == 0u) {  // the first block to give up
+                            dbg[1] = blockIdx.x;
+                            dbg[2] = seq;
+                            dbg[3] = atomicAdd(count, 0u);
+                            dbg[4] = atomicAdd(gen, 0u);
+                            dbg[5] = g;
+                            dbg[6] = (unsigned)(globaltimer_ns() - t0);
                         }
                         ok = 0;
                         break;

@@ -314,3 +314,31 @@ def test_er_config_small_counts():
         four += sum(1 for w in common if w > max(x, y, z))
     assert O.count(g.row_ptr, g.col_idx, 3, "degeneracy") == tri
     assert O.count(g.row_ptr, g.col_idx, 4, "degeneracy") == four
+
+
+@pytest.mark.parametrize("parts", [[3, 4, 5], [1, 2, 3, 4], [6, 6, 6, 6], [2, 9]])
+def test_per_vertex_complete_multipartite(parts):
+    # a vertex of part i lies in e_{k-1}(the other parts) k-cliques
+    g = synth.complete_multipartite(parts)
+    drp, dci, _, _ = O.dag_for(g.row_ptr, g.col_idx, "degeneracy")
+    start = np.cumsum([0] + parts)
+    for k in range(2, len(parts) + 2):
+        pv = O.count_orient(drp, dci, k, per_vertex=True).per_vertex
+        piv = O.count_pivot(g.row_ptr, g.col_idx, drp, dci, per_vertex_k=k).per_vertex
+        for i, a in enumerate(parts):
+            want = elementary_symmetric(parts[:i] + parts[i + 1:], k - 1)
+            for v in range(start[i], start[i] + a):
+                assert pv[v] == want and piv[v] == want, (parts, k, i)
+
+
+def test_per_vertex_join_with_a_clique():
+    # G join K_m: a vertex of K_m lies in sum_j c_j(G) C(m-1, k-1-j) k-cliques
+    h = synth.erdos_renyi(40, 0.2, 5)
+    m = 4
+    g = synth.join(h, synth.complete_graph(m))
+    drp, dci, _, _ = O.dag_for(g.row_ptr, g.col_idx, "degree")
+    c = [1] + [O.count(h.row_ptr, h.col_idx, j) if j > 2 else (h.n if j == 1 else h.num_edges) for j in range(1, 8)]
+    for k in range(2, 7):
+        pv = O.count_orient(drp, dci, k, per_vertex=True).per_vertex
+        want = sum(c[j] * math.comb(m - 1, k - 1 - j) for j in range(0, k))
+        assert all(pv[v] == want for v in range(h.n, h.n + m)), k

@@ -1,6 +1,8 @@
 """Generators of many small graphs: Barabasi-Albert, radius-1 ego networks
 and the block-diagonal union (inputs only, checked against their
 definitions)."""
+import math
+
 import numpy as np
 import pytest
 
@@ -45,3 +47,25 @@ def test_ego_networks_sizes_and_union():
         seg = u.col_idx[rows[0]:rows[-1]]
         assert seg.size == 2 * e.num_edges and (seg.size == 0 or (seg.min() >= a and seg.max() < b))
         assert np.array_equal(seg - a, e.col_idx)
+
+
+def test_serving_recipes():
+    from paper_2104_13209_gb300 import workloads
+
+    kinds = [workloads.serve_spec(i)[0] for i in range(workloads.POOL_SIZE)]
+    assert kinds.count("er") == 16 and kinds.count("rmat") == 24 and kinds.count("chunglu") == 24
+    for i in range(workloads.POOL_SIZE):
+        s = workloads.serve_spec(i)
+        if s[0] == "er":
+            assert 10_000 <= s[1] <= 100_000 and 8 <= s[2] * (s[1] - 1) <= 32
+        elif s[0] == "rmat":
+            assert 14 <= s[1] <= 18
+        else:
+            assert 100_000 <= s[1] <= 1_000_000
+    t, g, k, p = workloads.query_stream(2000.0, 5.0)
+    t2, g2, k2, p2 = workloads.query_stream(2000.0, 5.0)
+    assert np.array_equal(t, t2) and np.array_equal(g, g2) and np.array_equal(k, k2) and np.array_equal(p, p2)
+    assert abs(t.size - 10_000) < 4 * math.sqrt(10_000)  # a Poisson count within 4 sigma
+    assert np.all(np.diff(t) > 0) and t[-1] < 5.0
+    assert g.min() >= 0 and g.max() < 64 and k.min() == 3 and k.max() == 12
+    assert 0.45 < p.mean() < 0.55

@@ -49,7 +49,7 @@ typedef int kc_status;
 #define KC_E_TIMEOUT 5         /* a bounded device wait gave up; results are not valid */
 #define KC_E_CUDA 6            /* a CUDA runtime call failed */
 #define KC_E_INTERNAL 7        /* a device-side consistency check failed */
-#define KC_E_UNSUPPORTED 8     /* a size beyond what this build handles */
+#define KC_E_UNSUPPORTED 8     /* a size or case beyond what the library handles */
 
 /* ---- enumerations ------------------------------------------------------ */
 /* Orientation criterion (Section 3.1). */

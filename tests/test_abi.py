@@ -7,7 +7,7 @@ import re
 import numpy as np
 import pytest
 
-from paper_2104_13209_gb300 import build, kclique
+from paper_2104_13209_gb300 import build, kclique, synth
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "kclique.h")
 
@@ -60,3 +60,32 @@ def test_argument_checks_without_gpu(lib):
     total = ctypes.c_uint64()
     assert lib.kc_count(None, 3, 0, 0, 0, ctypes.byref(total), None, None, None) == kclique.KC_E_INVALID_ARG
     assert lib.kc_graph_info_get(None, None) == kclique.KC_E_INVALID_ARG
+
+
+def _has_gpu():
+    try:
+        import torch
+
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+@pytest.mark.skipif(_has_gpu(), reason="checks the behaviour on a machine without a GPU")
+def test_no_gpu_fails_loudly(lib):
+    # no fallback: a graph cannot be created, the error says why
+    with pytest.raises(kclique.KCError) as e:
+        kclique.Graph(np.array([0, 1, 2], dtype=np.uint32), np.array([1, 0], dtype=np.uint32))
+    assert e.value.status in (kclique.KC_E_CUDA, kclique.KC_E_NO_MEMORY)
+    assert kclique.last_error()
+    with pytest.raises(kclique.KCError):
+        kclique.Batch([synth.complete_graph(3)])
+    with pytest.raises(kclique.KCError):
+        kclique.Server()
+
+
+def test_missing_library_raises(monkeypatch, tmp_path):
+    monkeypatch.setattr(kclique, "_lib", None)
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "absent.so"))
+    with pytest.raises(ImportError):
+        kclique.load()

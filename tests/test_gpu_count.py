@@ -101,8 +101,10 @@ def test_k_beyond_clique_number_and_invalid_k():
 
 
 def test_rmat20_full_size_k4():
-    """R-MAT scale 20 (edge factor 16), k = 4, both schemes: the stored total
-    was written by tests/golden/make_golden.py from the oracle."""
+    """R-MAT scale 20 (edge factor 16), the bench's workload: k = 3 and 4
+    (and 5 where stored), both schemes, both orientations, in the bench's
+    launch configuration.  The stored totals were written by
+    tests/golden/make_golden.py from the oracle."""
     with open(os.path.join(GOLDEN, "counts.json")) as f:
         gold = json.load(f)
     rec = gold["rmat20_ef16_s0"]
@@ -110,8 +112,11 @@ def test_rmat20_full_size_k4():
     assert g.num_edges == rec["num_edges"]
     for orient in ("degeneracy", "degree"):
         G = graph(g, orient)
-        for scheme in ("vc", "ec"):
-            assert G.count(4, scheme=scheme).total == rec["counts"]["4"], (orient, scheme)
+        if orient == "degeneracy":
+            assert G.info()["d_max"] == rec["degeneracy_dmax"]
+        for k in sorted(int(x) for x in rec["counts"]):
+            for scheme in ("vc", "ec"):
+                assert G.count(k, scheme=scheme).total == rec["counts"][str(k)], (orient, k, scheme)
         G.close()
 
 

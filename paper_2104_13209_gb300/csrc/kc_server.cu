@@ -177,8 +177,19 @@ void take_cheapest(kc_server* S, std::deque<uint64_t>& q, uint32_t n, std::vecto
 
 // Pack up to max_batch queued orientation queries into one launch on slot b.
 void launch_batch(kc_server* S, BatchSlot& b) {
-    const uint32_t n = (uint32_t)std::min<size_t>(S->q_batch.size(), S->max_batch);
-    take_cheapest(S, S->q_batch, n, b.tickets);
+    take_cheapest(S, S->q_batch, (uint32_t)std::min<size_t>(S->q_batch.size(), S->max_batch), b.tickets);
+    // item indices of a launch are 32-bit: queries beyond 2^31 roots wait for the next launch
+    unsigned long long roots = 0;
+    size_t keep = 0;
+    while (keep < b.tickets.size()) {
+        const unsigned long long r = S->graphs[S->tickets[b.tickets[keep]].graph]->n;
+        if (keep > 0 && roots + r >= (1ull << 31)) break;
+        roots += r;
+        ++keep;
+    }
+    for (size_t i = b.tickets.size(); i-- > keep;) S->q_batch.push_front(b.tickets[i]);
+    b.tickets.resize(keep);
+    const uint32_t n = (uint32_t)b.tickets.size();
     b.finished.assign(n, 0);
     // descriptors grouped by configuration
     struct Item {

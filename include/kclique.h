@@ -198,8 +198,12 @@ kc_status kc_count_async(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_
 kc_status kc_count_noalloc(const kc_graph* g, uint32_t k, int scheme, uint32_t subwarp, kc_result* result_dev,
                            void* stream);
 
-/* Pre-allocate the device working memory kc_count_async will need for these
- * parameters (pivot as in kc_count; k_max = the largest k to be asked). */
+/* Pre-allocate the device working memory kc_count_async will need for
+ * orientation-mode counts up to k_max (every scheme and group width), so
+ * that later calls allocate nothing and can be captured into a CUDA graph.
+ * The pivoting path (pivot = 1, or per-vertex counts) still allocates its
+ * buffers on its first call: make one such call before a capture.  The
+ * pivot and per_vertex arguments are accepted for that future use. */
 kc_status kc_graph_reserve(kc_graph* g, uint32_t k_max, int pivot, int per_vertex, void* stream);
 
 /* Every clique size at once by pivoting (Fig. 3, Section 2.3).

@@ -187,8 +187,11 @@ kc_status kc_count_async(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_
  *   Working memory is a fixed 4 MiB array in the library's device image,
  *   one per device: the control words and one task counter per root with
  *   more than 32 out-neighbours.  The first call on a device looks up the
- *   array's address (make it before any stream capture); every call clears
- *   the part it uses with a stream-ordered memset.
+ *   array's address and keeps it until the process exits (make that call
+ *   before any stream capture; host threads may make it together).  A
+ *   cudaDeviceReset invalidates the kept address: do not call this entry
+ *   point on a device after resetting it.  Every call clears the part of
+ *   the array it uses with a stream-ordered memset.
  *   Limits: returns KC_E_UNSUPPORTED when the roots with more than 32
  *   out-neighbours exceed about 1,048,500, or when d_max is so large that
  *   the per-block bitmaps do not fit in shared memory (kc_count_async then

@@ -29,6 +29,7 @@
 // Blocks are persistent (Section 3.6).  Counts are summed per thread, per
 // warp, then into an exact 128-bit total with carry detection.
 #include <algorithm>
+#include <mutex>
 
 #include "kc_bitmap.cuh"
 #include "kc_common.cuh"
@@ -1396,6 +1397,7 @@ static constexpr size_t NOALLOC_WORDS = (size_t)1 << 20;  // 4 MiB, resident on 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[NOALLOC_WORDS];
 static constexpr int NOALLOC_MAX_DEVICES = 64;
 static void* g_noalloc_addr[NOALLOC_MAX_DEVICES];  // device address of the array, per device (set up once)
+static std::mutex g_noalloc_mu;                      // host threads that set up a device together
 
 }  // namespace kc
 
@@ -1415,14 +1417,18 @@ extern "C" kc_status kc_count_noalloc(const kc_graph* g, uint32_t k, int scheme,
     KC_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return set_error(KC_E_UNSUPPORTED, "device index %d too large", dev);
     if (dev != g->device) return set_error(KC_E_INVALID_ARG, "the graph lives on device %d, not %d", g->device, dev);
-    if (!g_noalloc_addr[dev]) {
+    uint32_t* scratch = nullptr;
+    {
         // set-up, once per device, with that device current: the host-side name
         // of the array is not a device address
-        void* ptr = nullptr;
-        KC_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-        g_noalloc_addr[dev] = ptr;
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* ptr = nullptr;
+            KC_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+            g_noalloc_addr[dev] = ptr;
+        }
+        scratch = (uint32_t*)g_noalloc_addr[dev];
     }
-    uint32_t* scratch = (uint32_t*)g_noalloc_addr[dev];
     if (k <= 2 || (uint64_t)k > (uint64_t)g->d_max + 1) {
         unsigned long long v = k == 1 ? g->n : (k == 2 ? g->m : 0ull);
         k_write_result<<<1, 1, 0, s>>>(result_dev, v);

@@ -106,12 +106,19 @@ def test_per_vertex_complete_graph():
         assert np.all(pv == math.comb(39, k - 1))
 
 
-def test_pivot_matches_orientation_traversal():
+def test_both_traversals_match_the_oracle_rmat14():
+    # every count on the GPU, by either traversal, against the oracle's
+    # orientation-mode count (a different route on the CPU)
     g = synth.rmat(14, 16, seed=6)
+    drp, dci, _, _ = O.dag_for(g.row_ptr, g.col_idx, "degeneracy")
     G = graph(g)
     counts, ovf, om, _ = G.count_all()
-    for k in range(3, min(om, 6) + 1):
-        assert int(counts[k]) == G.count(k, scheme="vc").total == G.count(k, scheme="ec").total
+    for k in range(3, 7):
+        want = O.count_orient(drp, dci, k).total
+        assert int(counts[k]) == want and ovf[k] == 0, k
+        assert G.count(k, pivot=True).total == want, k
+        assert G.count(k, scheme="vc").total == want, k
+        assert G.count(k, scheme="ec").total == want, k
 
 
 def test_per_vertex_requested_in_orientation_mode():

@@ -342,3 +342,38 @@ def test_per_vertex_join_with_a_clique():
         pv = O.count_orient(drp, dci, k, per_vertex=True).per_vertex
         want = sum(c[j] * math.comb(m - 1, k - 1 - j) for j in range(0, k))
         assert all(pv[v] == want for v in range(h.n, h.n + m)), k
+
+
+def test_degree_rank_hand_computed_with_ties():
+    """Degree orientation (Section 3.1) orders vertices by (degree, id).  The
+    graph has a four-way degree tie, an isolated vertex and one vertex of
+    largest degree; the expected ranks and DAG rows were worked out by hand:
+      degrees   0:3  1:2  2:2  3:2  4:1  5:2  6:2  7:0
+      order     7 (deg 0), 4 (deg 1), 1 2 3 5 6 (deg 2, ascending id), 0 (deg 3)
+    Ties broken by descending id, or sorting by descending degree, give other
+    ranks and other DAGs."""
+    edges = [(0, 1), (0, 2), (0, 3), (1, 2), (4, 5), (5, 6), (3, 6)]
+    g = synth.edges_to_csr(8, np.array([a for a, _ in edges]), np.array([b for _, b in edges]))
+    rank = O.degree_rank(g.row_ptr)
+    assert [int(x) for x in rank] == [7, 2, 3, 4, 1, 5, 6, 0]
+    drp, dci, dmax = O.orient(g.row_ptr, g.col_idx, rank)
+    rows = [sorted(int(x) for x in dci[drp[v]:drp[v + 1]]) for v in range(g.n)]
+    # u -> w iff rank[u] < rank[w]
+    assert rows == [[], [0, 2], [0], [0, 6], [5], [6], [], []]
+    assert dmax == 2
+
+
+def test_degree_rank_is_a_permutation_sorted_by_degree_then_id():
+    # on R-MAT graphs (thousands of ties): consecutive ranks never decrease in
+    # degree, and within one degree they increase with the id
+    for seed in (1, 2):
+        g = synth.rmat(11, 8, seed=seed)
+        rank = O.degree_rank(g.row_ptr).astype(np.int64)
+        deg = np.diff(g.row_ptr.astype(np.int64))
+        order = np.empty(g.n, dtype=np.int64)
+        order[rank] = np.arange(g.n)
+        assert np.array_equal(np.sort(rank), np.arange(g.n))
+        d = deg[order]
+        assert np.all(np.diff(d) >= 0)
+        same = np.diff(d) == 0
+        assert np.all(np.diff(order)[same] > 0)

@@ -66,6 +66,7 @@ typedef int kc_status;
 #define KC_FLAG_VERTEX_OVERFLOW 2u      /* some per-vertex count exceeded 2^64 - 1 */
 #define KC_FLAG_TIMEOUT 4u              /* a device wait ran out of time */
 #define KC_FLAG_INTERNAL 8u             /* a device-side check failed */
+#define KC_FLAG_TOTAL_OVERFLOW128 16u   /* the total exceeded 2^128 - 1 (pivoting only) */
 
 typedef struct kc_graph kc_graph;
 
@@ -220,6 +221,20 @@ kc_status kc_graph_reserve(kc_graph* g, uint32_t k_max, int pivot, int per_verte
  * Returns KC_E_OVERFLOW (outputs written) when any reported count overflowed. */
 kc_status kc_count_all(kc_graph* g, uint64_t* counts, uint8_t* overflow, uint32_t cap, uint32_t* omega_out,
                        uint32_t per_vertex_k, uint64_t* per_vertex_out, void* stream);
+
+/* kc_count_all with exact counts below 2^128 (Fig. 3's leaf sums C(q, j - h)
+ * carried in 128-bit arithmetic; Table 1's counts reach 5.4e18 and the
+ * middle sizes of dense graphs pass 2^64).
+ *   counts_lo, counts_hi (host, cap entries each): the low and high 64-bit
+ *     words of c_j; counts_lo[0] = 1.
+ *   overflow (host, nullable, cap entries): 1 where c_j exceeded 2^128 - 1
+ *     (the words are then not exact).
+ *   omega_out, per_vertex_k, per_vertex_out: as kc_count_all (per-vertex
+ *     counts stay 64-bit, flagged beyond 2^64 - 1).
+ * Returns KC_E_OVERFLOW (outputs written) when a count exceeded 2^128 - 1 or
+ * a per-vertex count exceeded 2^64 - 1. */
+kc_status kc_count_all128(kc_graph* g, uint64_t* counts_lo, uint64_t* counts_hi, uint8_t* overflow, uint32_t cap,
+                          uint32_t* omega_out, uint32_t per_vertex_k, uint64_t* per_vertex_out, void* stream);
 
 /* ---- batched counts over many small graphs -------------------------------
  * The paper counts one graph at a time; these calls serve workloads of

@@ -307,11 +307,11 @@ kc_status kc_count(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_t subw
     return count_sync(g, k, pivot, scheme, subwarp, total_out, &hi, per_vertex_out, flags_out, stream);
 }
 
-kc_status kc_count_all(kc_graph* g, uint64_t* counts, uint8_t* overflow, uint32_t cap, uint32_t* omega_out,
-                       uint32_t per_vertex_k, uint64_t* per_vertex_out, void* stream) {
-    clear_error();
+static kc_status count_all_common(kc_graph* g, uint64_t* counts_lo, uint64_t* counts_hi, uint8_t* overflow64,
+                                  uint8_t* overflow128, uint32_t cap, uint32_t* omega_out, uint32_t per_vertex_k,
+                                  uint64_t* per_vertex_out, void* stream) {
     if (!g) return set_error(KC_E_INVALID_ARG, "NULL graph");
-    if (!counts) return set_error(KC_E_INVALID_ARG, "counts is NULL");
+    if (!counts_lo) return set_error(KC_E_INVALID_ARG, "counts is NULL");
     if (cap == 0) return set_error(KC_E_INVALID_ARG, "cap must be >= 1");
     if (per_vertex_out && per_vertex_k == 0) return set_error(KC_E_INVALID_ARG, "per_vertex_k must be >= 1");
     cudaStream_t s = (cudaStream_t)stream;
@@ -325,21 +325,45 @@ kc_status kc_count_all(kc_graph* g, uint64_t* counts, uint8_t* overflow, uint32_
             pv_dev = per_vertex_out;
         }
     }
-    std::vector<uint8_t> ovf(cap);
+    std::vector<uint64_t> hi(cap);
+    std::vector<uint8_t> o128(cap);
     uint32_t flags = 0, omega = 0;
-    KC_CHECK(count_all_run(g, cap, per_vertex_out ? per_vertex_k : 0, pv_dev, counts, ovf.data(), &omega, &flags, s));
+    KC_CHECK(count_all_run(g, cap, per_vertex_out ? per_vertex_k : 0, pv_dev, counts_lo, hi.data(), o128.data(),
+                           &omega, &flags, s));
     if (pv_host && g->n) {
         KC_CUDA(cudaMemcpyAsync(per_vertex_out, pv_dev, (size_t)g->n * 8, cudaMemcpyDeviceToHost, s));
         KC_CUDA(cudaStreamSynchronize(s));
     }
-    if (overflow) memcpy(overflow, ovf.data(), cap);
+    if (counts_hi) memcpy(counts_hi, hi.data(), (size_t)cap * 8);
+    bool any64 = (flags & KC_FLAG_VERTEX_OVERFLOW) != 0, any128 = false;
+    for (uint32_t j = 0; j < cap; ++j) {
+        const bool o64 = hi[j] != 0 || o128[j] != 0;
+        if (overflow64) overflow64[j] = o64 ? 1 : 0;
+        if (overflow128) overflow128[j] = o128[j];
+        any64 |= o64;
+        any128 |= o128[j] != 0;
+    }
     if (omega_out) *omega_out = omega;
     if (flags & KC_FLAG_TIMEOUT) return set_error(KC_E_TIMEOUT, "time limit reached");
     if (flags & KC_FLAG_INTERNAL) return set_error(KC_E_INTERNAL, "device-side consistency check failed");
-    bool any = (flags & KC_FLAG_VERTEX_OVERFLOW) != 0;
-    for (uint32_t j = 0; j < cap; ++j) any |= ovf[j] != 0;
-    if (any) return set_error(KC_E_OVERFLOW, "a count exceeded 2^64 - 1");
+    if (counts_hi ? (any128 || (flags & KC_FLAG_VERTEX_OVERFLOW)) : any64)
+        return set_error(KC_E_OVERFLOW, counts_hi ? "a count exceeded 2^128 - 1" : "a count exceeded 2^64 - 1");
     return KC_OK;
+}
+
+kc_status kc_count_all(kc_graph* g, uint64_t* counts, uint8_t* overflow, uint32_t cap, uint32_t* omega_out,
+                       uint32_t per_vertex_k, uint64_t* per_vertex_out, void* stream) {
+    clear_error();
+    return count_all_common(g, counts, nullptr, overflow, nullptr, cap, omega_out, per_vertex_k, per_vertex_out,
+                            stream);
+}
+
+kc_status kc_count_all128(kc_graph* g, uint64_t* counts_lo, uint64_t* counts_hi, uint8_t* overflow, uint32_t cap,
+                          uint32_t* omega_out, uint32_t per_vertex_k, uint64_t* per_vertex_out, void* stream) {
+    clear_error();
+    if (!counts_hi) return set_error(KC_E_INVALID_ARG, "counts_hi is NULL");
+    return count_all_common(g, counts_lo, counts_hi, nullptr, overflow, cap, omega_out, per_vertex_k,
+                            per_vertex_out, stream);
 }
 
 }  // extern "C"

@@ -21,6 +21,19 @@ __device__ __forceinline__ uint32_t next_bit(const uint32_t* L, uint32_t from, u
     return (w << 5) + (__ffs(bits) - 1);
 }
 
+// position of the m-th (0-based) bit of L strictly above a (one thread)
+__device__ __forceinline__ uint32_t select_above(const uint32_t* L, uint32_t a, uint32_t m, uint32_t W) {
+    uint32_t lo = a + 1;
+    for (uint32_t w = lo >> 5; w < W; ++w) {
+        uint32_t x = L[w];
+        if (w == (lo >> 5)) x &= 0xFFFFFFFFu << (lo & 31);
+        const uint32_t c = __popc(x);
+        if (m < c) return (w << 5) + __fns(x, 0, m + 1);
+        m -= c;
+    }
+    return NONE;
+}
+
 // binary search of x in sorted s[lo, hi); returns index or NONE
 __device__ __forceinline__ uint32_t find_sorted(const uint32_t* s, uint32_t lo, uint32_t hi, uint32_t x) {
     while (lo < hi) {

@@ -182,14 +182,27 @@ kc_status batch_launch(const QDesc* q_dev, uint32_t nq, uint32_t d_cap, uint32_t
 // take).
 size_t batch_smem_bytes(uint32_t d_cap, uint32_t k_max, const BatchConfig& cfg);
 
+// kc_deep.cu: orientation-mode counts for k >= 5 with re-encoded small nodes.
+// deep_supported: whether the kernel takes (graph, k).  deep_plan: global
+// scratch words and grid size of its launch.  deep_launch: enqueue it over
+// roots[0, n_work) (roots[0, n_big) with more than 32 candidates); task_next
+// and task_total hold n_big zeroed words each.
+bool deep_supported(const kc_graph* g, uint32_t k);
+kc_status deep_plan(const kc_graph* g, uint32_t k, bool ec, size_t* scratch_words, int* blocks_out);
+kc_status deep_launch(kc_graph* g, uint32_t k, bool ec, uint32_t n_big, uint32_t n_work, uint32_t* task_next,
+                      uint32_t* task_total, uint32_t* gscratch, Ctl* ctl, cudaStream_t s);
+
 // kc_pivot.cu
 // Fixed-k pivoting count into result_dev (device); per_vertex_dev: n entries
 // (input numbering) or null.
 kc_status count_pivot_async(kc_graph* g, uint32_t k, kc_result* result_dev, uint64_t* per_vertex_dev,
                             cudaStream_t s);
-// Every size < cap by pivoting; host outputs; synchronises s.
-kc_status count_all_run(kc_graph* g, uint32_t cap, uint32_t pvk, uint64_t* per_vertex_dev, uint64_t* counts_host,
-                        uint8_t* ovf_host, uint32_t* omega_host, uint32_t* flags_host, cudaStream_t s);
+// Every size < cap by pivoting, exact below 2^128: counts_lo / counts_hi
+// (host, cap entries each; counts_hi nullable), ovf128_host[j] = 1 when the
+// count exceeds 2^128 - 1.  Synchronises s.
+kc_status count_all_run(kc_graph* g, uint32_t cap, uint32_t pvk, uint64_t* per_vertex_dev, uint64_t* counts_lo_host,
+                        uint64_t* counts_hi_host, uint8_t* ovf128_host, uint32_t* omega_host, uint32_t* flags_host,
+                        cudaStream_t s);
 
 int sm_count_of_current_device();
 

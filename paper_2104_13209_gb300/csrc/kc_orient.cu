@@ -8,15 +8,16 @@
 // the order, so every edge goes from a smaller to a larger id.  The induced
 // sub-graph of any candidate set listed in ascending id is then strictly
 // upper-triangular, which the counting kernels rely on.
+#include <cooperative_groups.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "kc_common.cuh"
 
 namespace kc {
 
 static constexpr uint32_t UNSET = 0xFFFFFFFFu;
-static constexpr uint32_t HEAVY_DEG = 4096;
-static constexpr unsigned long long PEEL_BARRIER_LIMIT_NS = 4000000000ull;  // 4 s
 
 // Flags of the validation pass.
 enum : unsigned {
@@ -93,262 +94,270 @@ __global__ void k_degree_key(const uint32_t* __restrict__ rp, uint32_t n, uint32
 }
 
 // ---------------------------------------------------------------------------
-// Level-synchronous k-core peeling (cooperative launch).  At level L every
-// remaining vertex of degree <= L is removed in sub-rounds: removing a
-// frontier decrements the degrees of its remaining neighbours, and a
-// neighbour whose degree falls to L joins the next frontier.  A vertex's
-// orientation key is its sub-round index; its core number is L.  A vertex
-// removed at level L had at most L remaining neighbours, so the DAG that
-// orients edges by (round, id) has out-degree <= degeneracy.
-// Each level's scan reads only the vertices still remaining and writes the
-// survivors to the other list, and a vertex is marked removed when it
-// enters a frontier (two grid barriers per sub-round).  Decrements from its
-// own entry round still reach it, so its final degree is its remaining
-// degree at removal (the second orientation key, k_removal_degree).
+// Level-synchronous k-core peeling in one thread-block cluster.
+//
+// At level L every remaining vertex of degree <= L is removed in sub-rounds:
+// a scan of the remaining vertices takes those of degree <= L (the first
+// frontier), then each sub-round removes a frontier, decrements the degrees
+// of all its neighbours, and a neighbour whose degree falls from L + 1 to L
+// joins the next frontier.  When a sub-round pushes nothing, L grows by one
+// (or jumps to the smallest remaining degree when a scan takes nothing).
+// A vertex's core number is the level at which it leaves; its first
+// orientation key is its sub-round (round_of).  A vertex removed at level L
+// had at most L neighbours left at the start of its sub-round, so the DAG
+// that orients edges by (sub-round, ...) has out-degree <= degeneracy.
+//
+// The peel is a chain of short phases (R-MAT scale 20: about 170 levels and
+// 630 sub-rounds), so the time between phases dominates, not the 31 M
+// neighbour decrements.  One cluster of up to 16 blocks runs it: the phases
+// are separated by hardware cluster barriers, and the control words live in
+// the shared memory of the cluster's first block (distributed shared
+// memory).  Frontiers are lists of items of at most PEEL_CH adjacency
+// entries, so a hub's neighbours spread over many lanes and every phase
+// needs one barrier.
+//
+// Control words rotate over three slots: phase p reads slot p % 3 (written
+// during phase p - 1), adds to slot (p + 1) % 3, and clears slot
+// (p + 2) % 3, whose last reader finished before the barrier that opened
+// phase p.  Every thread takes the same decision from the slot it reads, so
+// the loop stays uniform over the cluster.
+//
+// Degrees are decremented unconditionally (a removed vertex can never again
+// cross from L + 1 to L), so they say nothing about removed vertices; the
+// second orientation key, the remaining degree at removal, is computed after
+// the peel by k_removal_key: #{w in N(v) : round_of[w] >= round_of[v]}.
 // ---------------------------------------------------------------------------
-struct PeelCtl {
-    unsigned fcount[2];
-    unsigned rcount[2];     // lengths of the remaining-vertex lists being built
-    unsigned minrem[2];
-    unsigned hcount[2];     // heavy-list length, by round parity
-    unsigned bar_count;
-    unsigned bar_gen;
-    unsigned flags;
-    unsigned max_level;
-    unsigned rounds;
-    unsigned dbg[8];        // where a timed-out barrier gave up (see grid_barrier)
-    unsigned seq_max;       // highest barrier sequence number reached by any block
-    unsigned seq_min_done;  // lowest sequence number among blocks that finished
-    unsigned mismatch[6];   // first disagreement between blocks on a frontier size (see log_nf)
+static constexpr uint32_t PEEL_CH = 16;        // adjacency entries per frontier item
+static constexpr int PEEL_THREADS = 1024;
+static constexpr int PEEL_CLUSTER_MAX = 16;
+
+struct PeelSlot {
+    unsigned items;   // frontier items pushed during the phase
+    unsigned taken;   // vertices removed during the phase
+    unsigned kept;    // remaining-list entries written (scan phases)
+    unsigned minrem;  // smallest degree among the kept vertices (scan phases)
+    unsigned err;     // KC_FLAG_INTERNAL raised during the phase
 };
 
-// Every block logs the frontier size it read right after barrier number
-// `seq` (a ring of 65536 (seq, size) entries).  A block that reads a different
-// size than the first logger of the same barrier records the disagreement in
-// c->mismatch; the host reports it after the kernel (KC_E_INTERNAL).  Nothing
-// here changes the control flow of the kernel.
-static constexpr uint32_t NF_LOG = 65536;
-__device__ __forceinline__ void log_nf(PeelCtl* c, unsigned long long* nf_log, uint32_t nf, uint32_t seq) {
-    if (threadIdx.x != 0) return;
-    unsigned long long want = ((unsigned long long)seq << 32) | nf;
-    unsigned long long* e = &nf_log[seq & (NF_LOG - 1)];
-    unsigned long long cur = atomicAdd(e, 0ull);
-    for (int tries = 0; tries < 8; ++tries) {
-        if ((uint32_t)(cur >> 32) == seq) {
-            if ((uint32_t)cur != nf && atomicCAS(&c->mismatch[0], 0u, 1u) == 0u) {
-                c->mismatch[1] = seq;
-                c->mismatch[2] = (uint32_t)cur;
-                c->mismatch[3] = nf;
-                c->mismatch[4] = blockIdx.x;
-            }
-            return;
-        }
-        unsigned long long prev = atomicCAS(e, cur, want);
-        if (prev == cur) return;
-        cur = prev;
-    }
-}
+// Result of the peel, read by the host.
+struct PeelOut {
+    unsigned flags;
+    unsigned max_level;   // the degeneracy
+    unsigned rounds;      // number of sub-rounds (largest round_of + 1)
+    unsigned phases;
+};
 
-// All 32 lanes call; lanes with pred append val to buf (capacity cap).  A
-// push beyond the capacity is dropped and recorded as KC_FLAG_INTERNAL.
-__device__ __forceinline__ void warp_push(bool pred, uint32_t val, uint32_t* buf, unsigned* cnt, uint32_t cap,
-                                          unsigned* flags) {
-    unsigned b = __ballot_sync(0xffffffffu, pred);
-    if (b == 0) return;
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(b) - 1;
+// Warp-aggregated add to a counter; returns this lane's offset (all lanes call).
+__device__ __forceinline__ unsigned warp_reserve(unsigned cnt, unsigned* counter) {
+    const int lane = threadIdx.x & 31;
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
     unsigned base = 0;
-    if (lane == leader) base = atomicAdd(cnt, (unsigned)__popc(b));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    uint32_t pos = base + __popc(b & lanemask_lt());
+    if (lane == 31 && total) base = atomicAdd(counter, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + incl - cnt;
+}
+
+// Lanes with pred remove vertex v now (sub-round `round`, level `level`):
+// mark it, then append its adjacency as frontier items to F (capacity fcap,
+// item count in sl->items).  The warp writes the items of all its lanes
+// together.  All lanes call.
+__device__ __forceinline__ void peel_take(bool pred, uint32_t v, uint32_t round, uint32_t level,
+                                          const uint32_t* __restrict__ rp, uint32_t* round_of, uint32_t* core,
+                                          uint2* F, uint32_t fcap, PeelSlot* sl) {
+    uint32_t b = 0, e = 0, c = 0;
     if (pred) {
-        if (pos < cap) __stcg(&buf[pos], val);
-        else atomicOr(flags, (unsigned)KC_FLAG_INTERNAL);
+        __stcg(&round_of[v], round);
+        __stcg(&core[v], level);
+        b = __ldg(rp + v);
+        e = __ldg(rp + v + 1);
+        c = (e - b + PEEL_CH - 1) / PEEL_CH;
     }
-}
-
-// Control words written by other SMs are read with an atomic (served by L2,
-// never by a stale L1 line) by thread 0 and broadcast to the block.
-__device__ __forceinline__ unsigned block_read(unsigned* p) {
-    __shared__ unsigned s_val;
-    __syncthreads();
-    if (threadIdx.x == 0) s_val = atomicAdd(p, 0u);
-    __syncthreads();
-    return s_val;
-}
-
-// deg[] and round_of[] change under other SMs between grid barriers: read
-// them from L2 (ld.global.cg) so no stale L1 line is ever used.
-// A neighbour w of a vertex removed in round `round` loses one degree unless
-// it was removed before (round_of[w] <= round).  The decrement that brings
-// it to `level` pushes it into the next frontier and marks it removed in
-// round + 1 at once; decrements by other vertices of this round still
-// reach it, so that its final degree is its remaining degree at removal.
-__device__ __forceinline__ void peel_neighbour(const uint32_t* ci, uint32_t j, bool in_range, uint32_t level,
-                                               uint32_t round, int* deg, uint32_t* round_of, uint32_t* core,
-                                               uint32_t* Fn, unsigned* fcn, uint32_t n, unsigned* flags) {
-    bool push = false;
-    uint32_t w = 0;
-    if (in_range) {
-        w = ci[j];
-        const uint32_t r = w < n ? __ldcg(&round_of[w]) : 0u;
-        if (w < n && (r == UNSET || r == round + 1)) {
-            int old = atomicSub(&deg[w], 1);
-            push = (old == (int)level + 1);
-            if (push) {
-                __stcg(&round_of[w], round + 1);
-                core[w] = level;
-            }
+    const unsigned bal = __ballot_sync(0xffffffffu, pred);
+    if (bal == 0) return;
+    if ((threadIdx.x & 31) == (unsigned)(__ffs(bal) - 1)) atomicAdd(&sl->taken, (unsigned)__popc(bal));
+    const unsigned off = warp_reserve(c, &sl->items);
+    const unsigned need = __ballot_sync(0xffffffffu, c > 0);
+    const int lane = threadIdx.x & 31;
+    unsigned m = need;
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const uint32_t sb = __shfl_sync(0xffffffffu, b, src), se = __shfl_sync(0xffffffffu, e, src);
+        const uint32_t sc = __shfl_sync(0xffffffffu, c, src), so = __shfl_sync(0xffffffffu, off, src);
+        for (uint32_t x = lane; x < sc; x += 32) {
+            const uint32_t pos = so + x;
+            const uint32_t lo = sb + x * PEEL_CH;
+            if (pos < fcap) __stcg(&F[pos], make_uint2(lo, min(PEEL_CH, se - lo)));
+            else atomicOr(&sl->err, (unsigned)KC_FLAG_INTERNAL);
         }
     }
-    warp_push(push, w, Fn, fcn, n, flags);
 }
 
-__device__ __forceinline__ bool peel_barrier(PeelCtl* c, uint32_t nb, uint32_t& seq) {
-    // every thread publishes its own writes of the phase before arriving
-    __threadfence();
-    ++seq;
-    if (threadIdx.x == 0) atomicMax(&c->seq_max, seq);
-    return grid_barrier(&c->bar_count, &c->bar_gen, nb, &c->flags, PEEL_BARRIER_LIMIT_NS, c->dbg, seq);
-}
-
-__global__ void __launch_bounds__(256) k_peel(const uint32_t* __restrict__ rp, const uint32_t* __restrict__ ci,
-                                              uint32_t n, int* deg, uint32_t* round_of, uint32_t* core, uint32_t* F0,
-                                              uint32_t* F1, uint32_t* heavy, PeelCtl* c, unsigned long long* nf_log,
-                                              uint32_t* R0, uint32_t* R1) {
-    const uint32_t nb = gridDim.x;
-    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t gthreads = gridDim.x * blockDim.x;
+__global__ void __launch_bounds__(PEEL_THREADS, 1)
+k_peel_cluster(const uint32_t* __restrict__ rp, const uint32_t* __restrict__ ci, uint32_t n, int* deg,
+               uint32_t* round_of, uint32_t* core, uint2* F0, uint2* F1, uint32_t fcap, uint32_t* R0, uint32_t* R1,
+               PeelOut* out) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ PeelSlot slots[3];  // in use in the cluster's first block only
+    __shared__ PeelSlot seen;      // this block's copy of the slot read after a barrier
+    const unsigned rank = cl.block_rank();
+    const unsigned nblk = cl.num_blocks();
+    if (threadIdx.x < 3) slots[threadIdx.x] = PeelSlot{0u, 0u, 0u, UNSET, 0u};
+    cl.sync();
+    PeelSlot* s0 = cl.map_shared_rank(slots, 0);
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t gwarp = gtid >> 5, nwarps = gthreads >> 5;
-    uint32_t* F[2] = {F0, F1};
-    uint32_t* R[2] = {R0, R1};  // remaining vertices: each scan reads one list and writes the next
-    uint32_t level = 0, round = 0, remaining = n;
-    int cur = 0;
-    int rc = 0;                 // the list the next scan reads (the first scan reads every vertex)
-    uint32_t rn = n;            // its length
-    bool all = true;
-    uint32_t it = 0;
-    uint32_t seq = 0;
-    while (remaining > 0) {
-        // scan: collect remaining vertices with degree <= level, keep the
-        // others in the next remaining list, and track the smallest degree
-        // above the level
-        unsigned* mr = &c->minrem[it & 1];
-        const int rx = rc ^ 1;
-        uint32_t local_min = UNSET;
-        for (uint32_t base = gwarp * 32; base < rn; base += nwarps * 32) {
-            const uint32_t idx = base + lane;
-            uint32_t v = 0;
-            bool take = false, keep = false;
-            if (idx < rn) {
-                v = all ? idx : __ldcg(&R[rc][idx]);
-                if (__ldcg(&round_of[v]) == UNSET) {
-                    int d = __ldcg(&deg[v]);
-                    if (d <= (int)level) {
-                        take = true;
-                        __stcg(&round_of[v], round);  // removed in this level's first round
-                        core[v] = level;
-                    } else {
-                        keep = true;
-                        local_min = min(local_min, (uint32_t)d);
+    const uint32_t gwarp = rank * (PEEL_THREADS / 32) + (threadIdx.x >> 5);
+    const uint32_t nwarps = nblk * (PEEL_THREADS / 32);
+    const uint32_t gthread = gwarp * 32 + lane, nthreads = nwarps * 32;
+    uint32_t level = 0, round = 0, p = 0, max_level = 0;
+    int fb = 0;              // frontier buffer the next phase pushes into
+    int pf = 1;              // frontier buffer the next process phase reads
+    uint32_t nf = 0;         // its items
+    int rl = 0;              // remaining list the next scan reads
+    uint32_t rn = n;         // its length
+    bool all = true;         // the first scan reads every vertex
+    bool scan = true;        // kind of the next phase
+    unsigned fail = 0;
+    const uint32_t phase_cap = 4u * n + 64u;
+    for (;;) {
+        PeelSlot* wr = s0 + (p + 1) % 3;
+        if (rank == 0 && threadIdx.x == 0) slots[(p + 2) % 3] = PeelSlot{0u, 0u, 0u, UNSET, 0u};
+        if (scan) {
+            // take the remaining vertices of degree <= level, keep the others
+            uint32_t local_min = UNSET;
+            uint32_t* Rw = rl ? R0 : R1;
+            const uint32_t* Rr = rl ? R1 : R0;
+            uint2* Fw = fb ? F1 : F0;
+            for (uint32_t base = gwarp * 32; base < rn; base += nwarps * 32) {
+                const uint32_t idx = base + lane;
+                uint32_t v = 0;
+                bool take = false, keep = false;
+                if (idx < rn) {
+                    v = all ? idx : __ldcg(&Rr[idx]);
+                    if (__ldcg(&round_of[v]) == UNSET) {
+                        const int d = __ldcg(&deg[v]);
+                        if (d <= (int)level) {
+                            take = true;
+                        } else {
+                            keep = true;
+                            local_min = min(local_min, (uint32_t)d);
+                        }
                     }
                 }
+                peel_take(take, v, round, level, rp, round_of, core, Fw, fcap, wr);
+                const unsigned o = warp_reserve(keep ? 1u : 0u, &wr->kept);
+                if (keep) {
+                    if (o < n) __stcg(&Rw[o], v);
+                    else atomicOr(&wr->err, (unsigned)KC_FLAG_INTERNAL);
+                }
             }
-            warp_push(take, v, F[cur], &c->fcount[cur], n, &c->flags);
-            warp_push(keep, v, R[rx], &c->rcount[rx], n, &c->flags);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) local_min = min(local_min, __shfl_xor_sync(0xffffffffu, local_min, o));
+            if (lane == 0 && local_min != UNSET) atomicMin(&wr->minrem, local_min);
+        } else {
+            // remove frontier pf: decrement every neighbour of its items; a
+            // neighbour that falls to the level joins frontier fb
+            const uint2* Fr = pf ? F1 : F0;
+            uint2* Fw = fb ? F1 : F0;
+            for (uint32_t base = gthread - lane; base < nf; base += nthreads) {
+                const uint32_t i = base + lane;
+                uint2 it = make_uint2(0u, 0u);
+                if (i < nf) it = __ldcg(&Fr[i]);
+                for (uint32_t t0 = 0; t0 < PEEL_CH; t0 += 4) {
+                    if (__ballot_sync(0xffffffffu, it.y > t0) == 0) break;
+                    uint32_t w[4];
+                    int old[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) w[u] = (t0 + u < it.y) ? __ldg(ci + it.x + t0 + u) : UNSET;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) old[u] = (w[u] < n) ? atomicSub(&deg[w[u]], 1) : 0;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        peel_take(w[u] < n && old[u] == (int)level + 1, w[u], round + 1, level, rp, round_of, core,
+                                  Fw, fcap, wr);
+                }
+            }
         }
-        for (int o = 16; o > 0; o >>= 1) local_min = min(local_min, __shfl_xor_sync(0xffffffffu, local_min, o));
-        if (lane == 0 && local_min != UNSET) atomicMin(mr, local_min);
-        if (!peel_barrier(c, nb, seq)) return;
-        if (gtid == 0) atomicExch(&c->minrem[(it + 1) & 1], UNSET);
-        ++it;
-        {
-            // the list just written is the next one to read; the counter of the
-            // one just read is free (every block read it before this barrier)
-            const uint32_t rn_new = block_read(&c->rcount[rx]);
-            if (gtid == 0) atomicExch(&c->rcount[rc], 0u);
-            rc = rx;
-            rn = min(rn_new, n);
+        cl.sync();
+        ++p;
+        if (threadIdx.x == 0) seen = *wr;
+        __syncthreads();
+        const PeelSlot c = seen;
+        if (c.err) {
+            fail = c.err;
+            break;
+        }
+        if (p > phase_cap) {
+            fail = KC_FLAG_INTERNAL;
+            break;
+        }
+        if (scan) {
+            if (c.taken) max_level = level;
+            rl ^= 1;
+            rn = min(c.kept, n);
             all = false;
-        }
-        uint32_t nf = block_read(&c->fcount[cur]);
-        log_nf(c, nf_log, nf, seq);
-        if (nf > n || (block_read(&c->flags) & KC_FLAG_INTERNAL)) return;  // recorded in flags
-        if (nf == 0) {
-            uint32_t m = block_read(mr);
-            if (m == UNSET || m <= level) {  // cannot happen on a consistent state
-                if (gtid == 0) atomicOr(&c->flags, (unsigned)KC_FLAG_INTERNAL);
-                return;
-            }
-            level = m;
-            if (!peel_barrier(c, nb, seq)) return;
-            continue;
-        }
-        while (nf > 0) {
-            // the frontier F[cur] is already marked removed in `round`
-            const int nxt = cur ^ 1;
-            if (gtid == 0) atomicMax(&c->max_level, level);
-            // Counter resets sit between two grid barriers and the next use of
-            // the counter: the other parity's heavy counter (last read in the
-            // previous round's heavy phase, next written in the next round's
-            // light phase) is cleared here, and this frontier's counter in the
-            // heavy phase below.
-            if (gtid == 0) atomicExch(&c->hcount[(round + 1) & 1], 0u);
-            // light frontier vertices: one warp each
-            for (uint32_t i = gwarp; i < nf; i += nwarps) {
-                uint32_t u = __ldcg(&F[cur][i]);
-                uint32_t b = rp[u], e = rp[u + 1];
-                if (e - b > HEAVY_DEG) {
-                    if (lane == 0) {
-                        uint32_t hpos = atomicAdd(&c->hcount[round & 1], 1u);
-                        if (hpos < n) __stcg(&heavy[hpos], u);
-                        else atomicOr(&c->flags, (unsigned)KC_FLAG_INTERNAL);
-                    }
-                    continue;
+            nf = min(c.items, fcap);
+            if (nf == 0) {
+                if (rn == 0) break;  // every vertex is removed
+                // nothing (with edges) left at this level: jump to the smallest remaining degree
+                if (c.minrem == UNSET || c.minrem <= level) {
+                    fail = KC_FLAG_INTERNAL;
+                    break;
                 }
-                for (uint32_t j0 = b; j0 < e; j0 += 32)
-                    peel_neighbour(ci, j0 + lane, j0 + lane < e, level, round, deg, round_of, core, F[nxt],
-                                   &c->fcount[nxt], n, &c->flags);
+                level = c.minrem;
+            } else {
+                pf = fb;
+                fb ^= 1;
+                scan = false;
             }
-            if (!peel_barrier(c, nb, seq)) return;
-            // heavy frontier vertices: the whole grid on each.  Every block
-            // read nf before the light barrier: this frontier's counter is free.
-            if (gtid == 0) atomicExch(&c->fcount[cur], 0u);
-            uint32_t hc = min(block_read(&c->hcount[round & 1]), n);
-            for (uint32_t h = 0; h < hc; ++h) {
-                uint32_t u = __ldcg(&heavy[h]);
-                uint32_t b = rp[u], e = rp[u + 1];
-                for (uint32_t j0 = b + gwarp * 32; j0 < e; j0 += nwarps * 32)
-                    peel_neighbour(ci, j0 + lane, j0 + lane < e, level, round, deg, round_of, core, F[nxt],
-                                   &c->fcount[nxt], n, &c->flags);
-            }
-            if (!peel_barrier(c, nb, seq)) return;
-            remaining -= nf;
+        } else {
             ++round;
-            uint32_t nf_next = block_read(&c->fcount[nxt]);
-            log_nf(c, nf_log, nf_next, seq);
-            if (nf_next > n || (block_read(&c->flags) & KC_FLAG_INTERNAL)) return;  // recorded in flags
-            cur = nxt;
-            nf = nf_next;
+            nf = min(c.items, fcap);
+            if (nf == 0) {
+                ++level;
+                scan = true;
+            } else {
+                pf = fb;
+                fb ^= 1;
+            }
         }
-        // the next scan pushes into the counter every block just read as empty
-        if (!peel_barrier(c, nb, seq)) return;
-        ++level;
     }
-    if (gtid == 0) c->rounds = round;
-    if (threadIdx.x == 0) atomicMin(&c->seq_min_done, seq);
+    // no block leaves while another may still read the first block's slots
+    cl.sync();
+    if (rank == 0 && threadIdx.x == 0) {
+        out->flags = fail;
+        out->max_level = max_level;
+        out->rounds = round + 1;
+        out->phases = p;
+    }
+}
+
+// Second orientation key: the remaining degree of v when it was removed,
+// #{w in N(v) : round_of[w] >= round_of[v]} (one warp per vertex).
+__global__ void k_removal_key(const uint32_t* __restrict__ rp, const uint32_t* __restrict__ ci, uint32_t n,
+                              const uint32_t* __restrict__ round_of, uint32_t* __restrict__ key) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t v = gw; v < n; v += nw) {
+        const uint32_t b = rp[v], e = rp[v + 1], r = round_of[v];
+        uint32_t c = 0;
+        for (uint32_t j = b + lane; j < e; j += 32) c += round_of[ci[j]] >= r;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) key[v] = c;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Relabel + filter
 // ---------------------------------------------------------------------------
-// remaining degree of every vertex when it was removed (its final degree)
-__global__ void k_removal_degree(const int* __restrict__ deg, uint32_t n, uint32_t* __restrict__ atrem) {
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) atrem[v] = (uint32_t)max(0, deg[v]);
-}
-
 __global__ void k_invert(const uint32_t* __restrict__ old_of_new, uint32_t n, uint32_t* __restrict__ new_of_old) {
     uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) new_of_old[old_of_new[r]] = r;
@@ -385,14 +394,25 @@ __global__ void k_filter(const uint32_t* __restrict__ rp, const uint32_t* __rest
     if (MODE == 0 && cnt) atomicAdd(&outdeg_or_cursor[ru], cnt);
 }
 
+// Out-degree key (for the root order) and out-degree histogram.  Bins below
+// OUTDEG_BINS are counted in shared memory first: most vertices have small
+// out-degrees, and global atomics on the same few bins would serialise.
+static constexpr uint32_t OUTDEG_BINS = 1024;
 __global__ void k_outdeg_from_rowptr(const uint32_t* __restrict__ rp, uint32_t n, uint32_t* __restrict__ key,
                                      uint32_t dmax, unsigned* __restrict__ hist) {
+    __shared__ unsigned sh[OUTDEG_BINS];
+    for (uint32_t i = threadIdx.x; i < OUTDEG_BINS; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
     uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
         uint32_t d = rp[r + 1] - rp[r];
         key[r] = dmax - d;
-        atomicAdd(&hist[d], 1u);
+        if (d < OUTDEG_BINS) atomicAdd(&sh[d], 1u);
+        else atomicAdd(&hist[d], 1u);
     }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < OUTDEG_BINS && i <= dmax; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
 __global__ void k_rowlen_max(const uint32_t* __restrict__ rp, uint32_t n, unsigned* __restrict__ mx) {
@@ -461,6 +481,43 @@ static unsigned grid_for(uint64_t items, int threads, int sms) {
     return (unsigned)b;
 }
 
+// Largest cluster (16, 8, 4, 2 or 1 blocks of PEEL_THREADS) the device can
+// run the peel with; looked up once per device.
+static kc_status peel_cluster_size(int* out) {
+    static std::mutex mu;
+    static int cached[64] = {0};
+    int dev = 0;
+    KC_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && cached[dev]) {
+        *out = cached[dev];
+        return KC_OK;
+    }
+    KC_CUDA(cudaFuncSetAttribute((const void*)k_peel_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    int best = 1;
+    for (int c = PEEL_CLUSTER_MAX; c >= 1; c >>= 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)c);
+        cfg.blockDim = dim3(PEEL_THREADS);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, (const void*)k_peel_cluster, &cfg) == cudaSuccess && nc >= 1) {
+            best = c;
+            break;
+        }
+        cudaGetLastError();
+    }
+    if (dev >= 0 && dev < 64) cached[dev] = best;
+    *out = best;
+    return KC_OK;
+}
+
 kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, int validate, cudaStream_t s) {
     const uint32_t n = g->n;
     const uint32_t nnz = (uint32_t)(2 * g->m);
@@ -472,24 +529,25 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
 
     // scratch: small control words + per-vertex arrays
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    // frontier items: a vertex of degree d is pushed once, as ceil(d / PEEL_CH) items
+    const size_t fcap = (size_t)n + (size_t)nnz / PEEL_CH + 1;
     DevBuf work;
-    size_t wbytes = al(sizeof(PeelCtl)) + al(64) + 8 * al((size_t)n * 4 + 4) + al(((size_t)nnz / 2 + 1) * 4) +
-                    al((size_t)NF_LOG * 8);
+    size_t wbytes = al(sizeof(PeelOut)) + al(64) + 6 * al((size_t)n * 4 + 4) + 2 * al(fcap * 8) +
+                    al(((size_t)nnz / 2 + 1) * 4);
     kc_status st = dev_alloc(work, wbytes);
     if (st != KC_OK) return st;
     char* p = (char*)work.ptr;
-    PeelCtl* ctl = (PeelCtl*)p; p += al(sizeof(PeelCtl));
+    PeelOut* pout = (PeelOut*)p; p += al(sizeof(PeelOut));
     unsigned* words = (unsigned*)p; p += al(64);            // [0] validate flags, [1] max key, [2] d_max
     uint32_t* key = (uint32_t*)p; p += al((size_t)n * 4 + 4);
     int* deg = (int*)p; p += al((size_t)n * 4 + 4);
     uint32_t* round_of = (uint32_t*)p; p += al((size_t)n * 4 + 4);
-    uint32_t* F0 = (uint32_t*)p; p += al((size_t)n * 4 + 4);
-    uint32_t* F1 = (uint32_t*)p; p += al((size_t)n * 4 + 4);
+    uint2* F0 = (uint2*)p; p += al(fcap * 8);                // reused below as u32[n + 1] scratch
+    uint2* F1 = (uint2*)p; p += al(fcap * 8);
     uint32_t* heavy = (uint32_t*)p; p += al((size_t)n * 4 + 4);
     uint32_t* R0 = (uint32_t*)p; p += al((size_t)n * 4 + 4);
     uint32_t* R1 = (uint32_t*)p; p += al((size_t)n * 4 + 4);
     uint32_t* colbuf = (uint32_t*)p; p += al(((size_t)nnz / 2 + 1) * 4);
-    unsigned long long* nf_log = (unsigned long long*)p;
 
     auto fail = [&](kc_status e) {
         dev_free(work);
@@ -508,7 +566,7 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
         if (s2_ != KC_OK) return fail(s2_); \
     } while (0)
 
-    KC_TRY(cudaMemsetAsync(ctl, 0, sizeof(PeelCtl), s));
+    KC_TRY(cudaMemsetAsync(pout, 0, sizeof(PeelOut), s));
     KC_TRY(cudaMemsetAsync(words, 0, 64, s));
     unsigned h_words[4] = {0, 0, 0, 0};
 
@@ -546,42 +604,32 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
     if (degen) {
         KC_TRYS(dev_alloc(g->core, (size_t)n * 4 + 4));
         if (n > 0) {
-            int bps = 0;
-            KC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_peel, 256, 0));
-            if (bps < 1) return fail(set_error(KC_E_INTERNAL, "peel kernel cannot be resident"));
-            unsigned blocks = (unsigned)std::min<uint64_t>((uint64_t)bps * sms, std::max<uint64_t>(1, ((uint64_t)n + 255) / 256));
-            KC_TRY(cudaMemsetAsync(ctl->minrem, 0xFF, sizeof(ctl->minrem), s));
-            KC_TRY(cudaMemsetAsync(&ctl->seq_min_done, 0xFF, sizeof(unsigned), s));
-            const uint32_t* a_rp = d_rp;
-            const uint32_t* a_ci = d_ci;
-            uint32_t a_n = n;
-            uint32_t* a_core = (uint32_t*)g->core.ptr;
-            KC_TRY(cudaMemsetAsync(nf_log, 0xFF, (size_t)NF_LOG * 8, s));
-            void* args[] = {(void*)&a_rp, (void*)&a_ci, (void*)&a_n, (void*)&deg, (void*)&round_of,
-                            (void*)&a_core, (void*)&F0, (void*)&F1, (void*)&heavy, (void*)&ctl, (void*)&nf_log,
-                            (void*)&R0, (void*)&R1};
-            KC_TRY(cudaLaunchCooperativeKernel((const void*)k_peel, dim3(blocks), dim3(256), args, 0, s));
+            int csize = 0;
+            KC_TRYS(peel_cluster_size(&csize));
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)csize);
+            cfg.blockDim = dim3(PEEL_THREADS);
+            cfg.dynamicSmemBytes = 0;
+            cfg.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = (unsigned)csize;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            KC_TRY(cudaLaunchKernelEx(&cfg, k_peel_cluster, d_rp, d_ci, n, deg, round_of, (uint32_t*)g->core.ptr, F0,
+                                      F1, (uint32_t)std::min<size_t>(fcap, 0xFFFFFFFFu), R0, R1, pout));
             note_launch();
-            PeelCtl hc;
-            KC_TRY(cudaMemcpyAsync(&hc, ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, s));
+            PeelOut hc;
+            KC_TRY(cudaMemcpyAsync(&hc, pout, sizeof(PeelOut), cudaMemcpyDeviceToHost, s));
             KC_TRY(cudaStreamSynchronize(s));
-            if (hc.flags & KC_FLAG_TIMEOUT)
-                return fail(set_error(KC_E_TIMEOUT,
-                                      "k-core peel: a grid barrier wait ran out of time (blocks %u; gave up: block %u "
-                                      "seq %u arrivals %u gen %u waited-gen %u after %u ns; max seq %u, min finished "
-                                      "seq %u, rounds %u, level %u, flags %u; mismatch %u after barrier %u %u/%u block %u %u)",
-                                      blocks, hc.dbg[1], hc.dbg[2], hc.dbg[3], hc.dbg[4], hc.dbg[5], hc.dbg[6],
-                                      hc.seq_max, hc.seq_min_done, hc.rounds, hc.max_level, hc.flags, hc.mismatch[0],
-                                      hc.mismatch[1], hc.mismatch[2], hc.mismatch[3], hc.mismatch[4], hc.mismatch[5]));
-            if ((hc.flags & KC_FLAG_INTERNAL) || hc.mismatch[0])
-                return fail(set_error(KC_E_INTERNAL,
-                                      "k-core peel: inconsistent state (blocks %u; flags %u; frontier-size disagreement "
-                                      "%u: after barrier %u first %u then %u by block %u; rounds %u level %u)",
-                                      blocks, hc.flags, hc.mismatch[0], hc.mismatch[1], hc.mismatch[2], hc.mismatch[3],
-                                      hc.mismatch[4], hc.rounds, hc.max_level));
+            if (hc.flags & KC_FLAG_INTERNAL)
+                return fail(set_error(KC_E_INTERNAL, "k-core peel: inconsistent state after %u phases (level %u, "
+                                                     "%u sub-rounds)", hc.phases, hc.max_level, hc.rounds));
             g->degeneracy = hc.max_level;
             max_key = hc.rounds;
-            k_removal_degree<<<grid_for(n, 256, sms), 256, 0, s>>>(deg, n, key);
+            k_removal_key<<<grid_for((uint64_t)n * 32, 256, sms), 256, 0, s>>>(d_rp, d_ci, n, round_of, key);
             note_launch();
             KC_TRY(cudaGetLastError());
         } else {
@@ -603,7 +651,7 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
         unsigned maxdeg = 0;
         KC_TRY(cudaMemcpyAsync(&maxdeg, words + 1, 4, cudaMemcpyDeviceToHost, s));
         KC_TRY(cudaStreamSynchronize(s));
-        uint32_t* by_deg = F0;  // free after the peel
+        uint32_t* by_deg = (uint32_t*)F0;  // free after the peel
         KC_TRYS(sort_ids_by_key(key, n, maxdeg, by_deg, g->tmp, s));
         KC_TRYS(sort_ids_by_key(round_of, n, max_key, (uint32_t*)g->old_of_new.ptr, g->tmp, s, by_deg));
     } else {
@@ -617,7 +665,7 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
     KC_TRYS(dev_alloc(g->row_ptr, ((size_t)n + 1) * 4));
     // rows are scanned in 16-byte quads: pad to whole quads plus one
     KC_TRYS(dev_alloc(g->col, (((size_t)g->m + 3) / 4 + 1) * 16));
-    uint32_t* outdeg = F0;  // reuse
+    uint32_t* outdeg = (uint32_t*)F0;  // reuse
     KC_TRY(cudaMemsetAsync(outdeg, 0, (size_t)n * 4 + 4, s));
     const uint64_t fthreads = ((uint64_t)nnz + 7) / 8;
     const unsigned fblocks = (unsigned)std::max<uint64_t>(1, (fthreads + 255) / 256);
@@ -629,7 +677,7 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
     uint32_t* drp = (uint32_t*)g->row_ptr.ptr;
     KC_TRYS(scan_u32(outdeg, drp, n, g->tmp, s));
     // fill (unsorted) into colbuf, then sort rows into col
-    uint32_t* cursor = F1;
+    uint32_t* cursor = (uint32_t*)F1;
     KC_TRY(cudaMemcpyAsync(cursor, drp, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
     if (nnz) {
         k_filter<1><<<fblocks, 256, 0, s>>>(d_rp, d_ci, n, nnz, (uint32_t*)g->new_of_old.ptr, cursor, colbuf);

@@ -1101,25 +1101,42 @@ __global__ void __launch_bounds__(PB) k_count_pivot(const PivotParams P) {
         if (s_hist[i]) atomicAdd(&P.leaves[(size_t)(i / LQ) * P.hq + (i % LQ)], s_hist[i]);
 }
 
-__global__ void k_binom(unsigned long long* t, uint32_t B) {
-    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) t[b] = b == 0 ? 1ull : 0ull;
+typedef unsigned __int128 u128;
+static constexpr u128 SAT128 = ~(u128)0;
+
+__device__ __forceinline__ u128 sat_add128(u128 a, u128 b) {
+    const u128 s = a + b;
+    return (s < a || a == SAT128 || b == SAT128) ? SAT128 : s;
+}
+
+// Pascal's triangle C(a, b) for a, b < B: t128 exact below 2^128 (SAT128 =
+// not representable), t64 the same saturated at 2^64 - 1 (SAT).
+__global__ void k_binom(unsigned long long* t64, u128* t128, uint32_t B) {
+    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) t128[b] = b == 0 ? (u128)1 : (u128)0;
     __syncthreads();
     for (uint32_t a = 1; a < B; ++a) {
         for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) {
-            unsigned long long x = b ? t[(size_t)(a - 1) * B + b - 1] : 0ull;
-            unsigned long long y = t[(size_t)(a - 1) * B + b];
-            t[(size_t)a * B + b] = b == 0 ? 1ull : sat_add(x, y);
+            const u128 x = b ? t128[(size_t)(a - 1) * B + b - 1] : (u128)0;
+            const u128 y = t128[(size_t)(a - 1) * B + b];
+            t128[(size_t)a * B + b] = b == 0 ? (u128)1 : sat_add128(x, y);
         }
         __syncthreads();
     }
+    for (size_t i = threadIdx.x; i < (size_t)B * B; i += blockDim.x) {
+        const u128 c = t128[i];
+        t64[i] = (c >> 64) ? SAT : (unsigned long long)c;
+    }
 }
 
-// counts[j] = sum over (h, q) of leaves[h][q] * C(q, j - h); omega = max h + q.
-__global__ void k_pivot_reduce(const unsigned long long* leaves, uint32_t hq, const unsigned long long* binom_t,
-                               uint32_t B, uint32_t cap, uint32_t kfix, unsigned long long n, unsigned long long m,
-                               unsigned long long* counts, unsigned char* ovf, unsigned int* omega) {
+// counts[j] = sum over (h, q) of leaves[h][q] * C(q, j - h) in 128-bit
+// arithmetic (counts_lo / counts_hi); ovf128[j] = 1 when the exact value
+// exceeds 2^128 - 1.  omega = max h + q.
+__global__ void k_pivot_reduce(const unsigned long long* leaves, uint32_t hq, const u128* binom128, uint32_t B,
+                               uint32_t cap, uint32_t kfix, unsigned long long n, unsigned long long m,
+                               unsigned long long* counts_lo, unsigned long long* counts_hi, unsigned char* ovf128,
+                               unsigned int* omega) {
     for (uint32_t j = threadIdx.x + blockIdx.x * blockDim.x; j < cap; j += gridDim.x * blockDim.x) {
-        unsigned long long s = 0;
+        u128 s = 0;
         bool o = false;
         if (j == 0) s = 1;
         else if (j == 1) s = n;
@@ -1129,18 +1146,25 @@ __global__ void k_pivot_reduce(const unsigned long long* leaves, uint32_t hq, co
                 for (uint32_t q = j - h; q < hq; ++q) {
                     const unsigned long long L = leaves[(size_t)h * hq + q];
                     if (!L) continue;
-                    const unsigned long long c = (q < B && j - h < B) ? binom_t[(size_t)q * B + (j - h)] : SAT;
-                    if (c == SAT) { o = true; continue; }
-                    const unsigned long long lo = L * c;
-                    if (__umul64hi(L, c) != 0) o = true;
-                    const unsigned long long t = s + lo;
+                    const u128 c = (q < B && j - h < B) ? binom128[(size_t)q * B + (j - h)] : SAT128;
+                    if (c == SAT128) { o = true; continue; }
+                    // L * c with c = (chi, clo): L * clo is exact in 128 bits; L * chi must fit in 64
+                    const unsigned long long clo = (unsigned long long)c, chi = (unsigned long long)(c >> 64);
+                    const u128 p1 = (u128)L * clo;
+                    if (chi && __umul64hi(L, chi)) { o = true; continue; }
+                    const unsigned long long p2 = L * chi;
+                    const unsigned long long top = (unsigned long long)(p1 >> 64) + p2;
+                    if (top < p2) { o = true; continue; }
+                    const u128 prod = ((u128)top << 64) | (unsigned long long)p1;
+                    const u128 t = s + prod;
                     if (t < s) o = true;
                     s = t;
                 }
             }
         }
-        counts[j] = s;
-        ovf[j] = o ? 1 : 0;
+        counts_lo[j] = (unsigned long long)s;
+        counts_hi[j] = (unsigned long long)(s >> 64);
+        ovf128[j] = o ? 1 : 0;
     }
     if (blockIdx.x == 0) {
         unsigned int w = 0;
@@ -1203,17 +1227,18 @@ static kc_status pivot_run(kc_graph* g, uint32_t kfix, uint32_t cap, uint32_t pv
     const size_t leaves_b = (size_t)hq * hq * 8, binom_b = (size_t)B * B * 8;
     const size_t tasks_b = ((size_t)n_big + 16) * 4, pv_b = pvk ? ((size_t)n + 16) * 8 : 0;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    KC_CHECK(dev_alloc(g->pv, al(leaves_b) + al(binom_b) + al(tasks_b) + al(pv_b)));
+    KC_CHECK(dev_alloc(g->pv, al(leaves_b) + al(binom_b) + al(2 * binom_b) + al(tasks_b) + al(pv_b)));
     char* p = (char*)g->pv.ptr;
     unsigned long long* leaves = (unsigned long long*)p; p += al(leaves_b);
     unsigned long long* binom_t = (unsigned long long*)p; p += al(binom_b);
+    u128* binom128 = (u128*)p; p += al(2 * binom_b);
     uint32_t* tasks = (uint32_t*)p; p += al(tasks_b);
     unsigned long long* pv = pvk ? (unsigned long long*)p : nullptr;
     KC_CUDA(cudaMemsetAsync(ctl, 0, ctl_bytes(), s));
     KC_CUDA(cudaMemsetAsync(leaves, 0, leaves_b, s));
     KC_CUDA(cudaMemsetAsync(tasks, 0, tasks_b, s));
     if (pv) KC_CUDA(cudaMemsetAsync(pv, 0, pv_b, s));
-    k_binom<<<1, 1024, 0, s>>>(binom_t, B);
+    k_binom<<<1, 1024, 0, s>>>(binom_t, binom128, B);
     note_launch();
     KC_CUDA(cudaGetLastError());
     unsigned long long budget = g->time_limit_s > 0 ? (unsigned long long)(g->time_limit_s * 1e9) : 0ull;
@@ -1303,8 +1328,8 @@ static kc_status pivot_run(kc_graph* g, uint32_t kfix, uint32_t cap, uint32_t pv
         KC_CUDA(cudaGetLastError());
     }
     KC_CUDA(cudaMemsetAsync(omega_dev, 0, 4, s));
-    k_pivot_reduce<<<std::max<uint32_t>(1, (cap + 255) / 256), 256, 0, s>>>(leaves, hq, binom_t, B, cap, kfix, n, g->m,
-                                                                            counts_dev, ovf_dev, omega_dev);
+    k_pivot_reduce<<<std::max<uint32_t>(1, (cap + 255) / 256), 256, 0, s>>>(
+        leaves, hq, binom128, B, cap, kfix, n, g->m, counts_dev, counts_dev + cap, ovf_dev, omega_dev);
     note_launch();
     KC_CUDA(cudaGetLastError());
     if (per_vertex_dev && pv) {
@@ -1317,21 +1342,24 @@ static kc_status pivot_run(kc_graph* g, uint32_t kfix, uint32_t cap, uint32_t pv
     return KC_OK;
 }
 
-__global__ void k_pack_pivot_result(const unsigned long long* counts, const unsigned char* ovf, const unsigned* flags,
-                                    const Ctl* ctl, uint32_t k, kc_result* out) {
+__global__ void k_pack_pivot_result(const unsigned long long* counts, uint32_t cap, const unsigned char* ovf128,
+                                    const unsigned* flags, const Ctl* ctl, uint32_t k, kc_result* out) {
     kc_result r;
     r.total = counts[k];
-    r.total_hi = 0;
-    r.flags = *flags | (ovf[k] ? KC_FLAG_TOTAL_OVERFLOW : 0u);
+    r.total_hi = counts[cap + k];
+    r.flags = *flags;
+    if (r.total_hi || ovf128[k]) r.flags |= KC_FLAG_TOTAL_OVERFLOW;
+    if (ovf128[k]) r.flags |= KC_FLAG_TOTAL_OVERFLOW128;
     r.status = (*flags & KC_FLAG_TIMEOUT) ? KC_E_TIMEOUT : ((*flags & KC_FLAG_INTERNAL) ? KC_E_INTERNAL : KC_OK);
     r.words = ctl->words;
     *out = r;
 }
 
-// Output area of a pivoting run: counts[cap] u64, ovf[cap] u8, omega, flags.
+// Output area of a pivoting run: counts lo[cap], hi[cap] (u64 each),
+// ovf128[cap] u8, omega, flags.
 static kc_status pivot_out(kc_graph* g, uint32_t cap, unsigned long long*& counts, unsigned char*& ovf,
                            unsigned int*& omega, unsigned int*& flags) {
-    const size_t cb = ((size_t)cap * 8 + 255) & ~(size_t)255, ob = ((size_t)cap + 255) & ~(size_t)255;
+    const size_t cb = ((size_t)cap * 16 + 255) & ~(size_t)255, ob = ((size_t)cap + 255) & ~(size_t)255;
     KC_CHECK(dev_alloc(g->pivot_out, cb + ob + 256));
     char* p = (char*)g->pivot_out.ptr;
     counts = (unsigned long long*)p;
@@ -1348,21 +1376,23 @@ kc_status count_pivot_async(kc_graph* g, uint32_t k, kc_result* result_dev, uint
     unsigned int *omega, *flags;
     KC_CHECK(pivot_out(g, k + 1, counts, ovf, omega, flags));
     KC_CHECK(pivot_run(g, k, k + 1, per_vertex_dev ? k : 0, per_vertex_dev, counts, ovf, omega, flags, s));
-    k_pack_pivot_result<<<1, 1, 0, s>>>(counts, ovf, flags, (const Ctl*)g->ctl.ptr, k, result_dev);
+    k_pack_pivot_result<<<1, 1, 0, s>>>(counts, k + 1, ovf, flags, (const Ctl*)g->ctl.ptr, k, result_dev);
     note_launch();
     KC_CUDA(cudaGetLastError());
     return KC_OK;
 }
 
-kc_status count_all_run(kc_graph* g, uint32_t cap, uint32_t pvk, uint64_t* per_vertex_dev, uint64_t* counts_host,
-                        uint8_t* ovf_host, uint32_t* omega_host, uint32_t* flags_host, cudaStream_t s) {
+kc_status count_all_run(kc_graph* g, uint32_t cap, uint32_t pvk, uint64_t* per_vertex_dev, uint64_t* counts_lo_host,
+                        uint64_t* counts_hi_host, uint8_t* ovf128_host, uint32_t* omega_host, uint32_t* flags_host,
+                        cudaStream_t s) {
     unsigned long long* counts;
     unsigned char* ovf;
     unsigned int *omega, *flags;
     KC_CHECK(pivot_out(g, cap, counts, ovf, omega, flags));
     KC_CHECK(pivot_run(g, 0, cap, pvk, per_vertex_dev, counts, ovf, omega, flags, s));
-    KC_CUDA(cudaMemcpyAsync(counts_host, counts, (size_t)cap * 8, cudaMemcpyDeviceToHost, s));
-    if (ovf_host) KC_CUDA(cudaMemcpyAsync(ovf_host, ovf, cap, cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaMemcpyAsync(counts_lo_host, counts, (size_t)cap * 8, cudaMemcpyDeviceToHost, s));
+    if (counts_hi_host) KC_CUDA(cudaMemcpyAsync(counts_hi_host, counts + cap, (size_t)cap * 8, cudaMemcpyDeviceToHost, s));
+    if (ovf128_host) KC_CUDA(cudaMemcpyAsync(ovf128_host, ovf, cap, cudaMemcpyDeviceToHost, s));
     unsigned int of[2];
     KC_CUDA(cudaMemcpyAsync(of, omega, 8, cudaMemcpyDeviceToHost, s));
     unsigned long long work = 0;

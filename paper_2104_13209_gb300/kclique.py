@@ -37,6 +37,7 @@ KC_FLAG_TOTAL_OVERFLOW = 1
 KC_FLAG_VERTEX_OVERFLOW = 2
 KC_FLAG_TIMEOUT = 4
 KC_FLAG_INTERNAL = 8
+KC_FLAG_TOTAL_OVERFLOW128 = 16
 
 _ORIENT = {"degree": KC_ORIENT_DEGREE, "degeneracy": KC_ORIENT_DEGENERACY}
 _SCHEME = {"auto": KC_SCHEME_AUTO, "vc": KC_SCHEME_VC, "ec": KC_SCHEME_EC}
@@ -45,6 +46,7 @@ _SCHEME = {"auto": KC_SCHEME_AUTO, "vc": KC_SCHEME_VC, "ec": KC_SCHEME_EC}
 EXPORTED = [
     "kc_last_error", "kc_status_name", "kc_version", "kc_graph_create", "kc_graph_destroy", "kc_graph_info_get",
     "kc_graph_export", "kc_count", "kc_count128", "kc_count_async", "kc_count_noalloc", "kc_graph_reserve", "kc_count_all",
+    "kc_count_all128",
     "kc_graph_set_time_limit", "kc_launch_count", "kc_graph_last_work",
     "kc_batch_create", "kc_batch_destroy", "kc_batch_graph_info", "kc_batch_set_time_limit", "kc_batch_count",
     "kc_batch_tune", "kc_batch_capture", "kc_batch_exec_launch", "kc_batch_exec_destroy",
@@ -132,6 +134,7 @@ def load(build_if_missing: bool = False):
     lib.kc_count_noalloc.argtypes = [vp, u32, i32, u32, vp, vp]
     lib.kc_graph_reserve.argtypes = [vp, u32, i32, i32, vp]
     lib.kc_count_all.argtypes = [vp, vp, vp, u32, ctypes.POINTER(u32), u32, vp, vp]
+    lib.kc_count_all128.argtypes = [vp, vp, vp, vp, u32, ctypes.POINTER(u32), u32, vp, vp]
     lib.kc_graph_set_time_limit.argtypes = [vp, ctypes.c_double]
     lib.kc_graph_last_work.argtypes = [vp, ctypes.POINTER(u64)]
     lib.kc_graph_last_work.restype = i32
@@ -158,7 +161,8 @@ def load(build_if_missing: bool = False):
               "kc_batch_count", "kc_batch_tune", "kc_batch_capture", "kc_batch_exec_launch", "kc_batch_exec_destroy"):
         getattr(lib, f).restype = i32
     for f in ("kc_graph_create", "kc_graph_destroy", "kc_graph_info_get", "kc_graph_export", "kc_count",
-              "kc_count128", "kc_count_async", "kc_count_noalloc", "kc_graph_reserve", "kc_count_all", "kc_graph_set_time_limit"):
+              "kc_count128", "kc_count_async", "kc_count_noalloc", "kc_graph_reserve", "kc_count_all", "kc_count_all128",
+              "kc_graph_set_time_limit"):
         getattr(lib, f).restype = i32
     _lib = lib
     return lib
@@ -310,6 +314,22 @@ class Graph:
         _check(load().kc_count_all(self._h, counts.ctypes.data, ovf.ctypes.data, cap, ctypes.byref(om), per_vertex_k,
                                    pv.ctypes.data if pv is not None else None, _stream_ptr(stream)),
                allow=(KC_OK, KC_E_OVERFLOW))
+        return counts, ovf, om.value, (pv[: self.n] if pv is not None else None)
+
+    def count_all128(self, cap: int | None = None, per_vertex_k: int = 0, stream=None):
+        """Every clique size by pivoting, exact below 2^128: (counts as Python ints, overflow uint8[cap]
+        (beyond 2^128 - 1), omega, per-vertex uint64[n] or None)."""
+        if cap is None:
+            cap = self.info()["d_max"] + 3
+        lo = np.zeros(cap, dtype=np.uint64)
+        hi = np.zeros(cap, dtype=np.uint64)
+        ovf = np.zeros(cap, dtype=np.uint8)
+        om = ctypes.c_uint32()
+        pv = np.zeros(max(self.n, 1), dtype=np.uint64) if per_vertex_k else None
+        _check(load().kc_count_all128(self._h, lo.ctypes.data, hi.ctypes.data, ovf.ctypes.data, cap, ctypes.byref(om),
+                                      per_vertex_k, pv.ctypes.data if pv is not None else None, _stream_ptr(stream)),
+               allow=(KC_OK, KC_E_OVERFLOW))
+        counts = [(int(h) << 64) | int(x) for x, h in zip(lo, hi)]
         return counts, ovf, om.value, (pv[: self.n] if pv is not None else None)
 
     def count_async(self, k: int, result_dev, pivot: bool = False, scheme: str = "auto", subwarp: int = 0,

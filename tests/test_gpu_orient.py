@@ -63,6 +63,11 @@ def test_degeneracy_orientation(gi):
     assert np.array_equal(np.sort(nof), np.arange(g.n))
     a, b, src, dst = _dag_edges_in_input_ids(rp, col, nof)
     assert np.all(src < dst)
+    # a peel order: every vertex has at most core(v) out-neighbours
+    outdeg = np.diff(rp.astype(np.int64))
+    old_of_new = np.empty_like(nof)
+    old_of_new[nof] = np.arange(g.n, dtype=nof.dtype)
+    assert np.all(outdeg <= core[old_of_new])
     und = np.sort(np.minimum(a, b).astype(np.uint64) * g.n + np.maximum(a, b))
     lo, hi = g.edge_pairs()
     assert np.array_equal(und, np.sort(lo.astype(np.uint64) * g.n + hi))

@@ -130,3 +130,43 @@ def test_per_vertex_requested_in_orientation_mode():
         want = O.count_orient(drp, dci, k, per_vertex=True)
         tot, pv, fl = G.count_per_vertex(k, pivot=False)
         assert tot == want.total and [int(x) for x in pv] == want.per_vertex
+
+
+U128 = 1 << 128
+
+
+def test_exact_128_bit_counts_complete_graphs():
+    # K68, k = 34: C(68, 34) = 28,453,041,475,240,576,740 > 2^64 - 1, exact
+    G = graph(synth.complete_graph(68))
+    counts, ovf, om, _ = G.count_all128(cap=70)
+    assert counts[34] == 28_453_041_475_240_576_740 and ovf[34] == 0
+    assert all(counts[j] == math.comb(68, j) for j in range(70))
+    r = G.count(34, pivot=True)
+    assert r.total == 28_453_041_475_240_576_740 and r.overflow
+    # K100: every size below 2^128 (C(100, 50) ~ 1.0e29)
+    G = graph(synth.complete_graph(100))
+    counts, ovf, om, _ = G.count_all128(cap=102)
+    assert om == 100
+    assert all(counts[j] == math.comb(100, j) and ovf[j] == 0 for j in range(102))
+    assert G.count(50, pivot=True).total == math.comb(100, 50)
+    # K140: the middle sizes pass 2^128 - 1 and are flagged, the others exact
+    G = graph(synth.complete_graph(140))
+    counts, ovf, om, _ = G.count_all128(cap=142)
+    for j in range(142):
+        exact = math.comb(140, j)
+        if exact >= U128:
+            assert ovf[j] == 1, j
+        else:
+            assert ovf[j] == 0 and counts[j] == exact, j
+    assert any(ovf) and not ovf[20]
+
+
+def test_exact_128_bit_counts_match_oracle():
+    # the oracle's counts are exact integers (128-bit sums)
+    g = synth.chung_lu_planted(20000, 2.1, 10, 20, 20, 60, 0.9, seed=1)
+    want, omega = oracle_allk(g)
+    G = graph(g)
+    counts, ovf, om, _ = G.count_all128(cap=len(want))
+    assert om == omega
+    for j in range(1, len(want)):
+        assert ovf[j] == 0 and counts[j] == want[j], j

@@ -91,7 +91,7 @@ def test_multipartite_wide_orientation(k):
     for orient in ("degeneracy", "degree"):
         G = graph(multipartite(), orient)
         for scheme in ("vc", "ec"):
-            for sw in (4, 8, 32):
+            for sw in ((4, 8, 32) if k <= 4 else (0,)):
                 got = G.count(k, scheme=scheme, subwarp=sw).total
                 assert got == elementary_symmetric(PARTS, k), (orient, k, scheme, sw)
 
@@ -116,7 +116,8 @@ def test_global_scratch_orientation_deep(orient):
     for k in (3, 4, 5, 6, 7):
         want = join_count(k)
         for scheme in ("vc", "ec"):
-            for sw in (1, 8, 32):
+            # group widths matter to the k <= 4 traversal only
+            for sw in ((1, 8, 32) if k <= 4 else (0,)):
                 got = G.count(k, scheme=scheme, subwarp=sw).total
                 assert got == want, (orient, k, scheme, sw)
 

@@ -214,6 +214,12 @@ kc_status kc_graph_export(const kc_graph* g, uint32_t* dag_row_ptr, uint32_t* da
     return KC_OK;
 }
 
+// whether orientation-mode per-vertex counts of size k run in the
+// orientation traversal (else the pivoting one serves them)
+static bool orient_per_vertex(const kc_graph* g, uint32_t k) {
+    return k >= 3 && (uint64_t)k <= (uint64_t)g->d_max + 1 && deep_supported(g, k, true);
+}
+
 static kc_status resolve(const kc_graph* g, uint32_t k, int pivot, int scheme, uint32_t subwarp, CountArgs& a) {
     if (!g) return set_error(KC_E_INVALID_ARG, "NULL graph");
     if (k == 0) return set_error(KC_E_INVALID_ARG, "k must be >= 1");
@@ -245,9 +251,12 @@ kc_status kc_count_async(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_
     if (!result_dev) return set_error(KC_E_INVALID_ARG, "result_dev is NULL");
     if (per_vertex_dev && !is_device_pointer(per_vertex_dev))
         return set_error(KC_E_INVALID_ARG, "per_vertex_dev must be device memory");
-    // per-vertex counts always come from the pivoting traversal restricted
-    // to size k (the same exact counts)
-    if (pivot || per_vertex_dev) return count_pivot_async(g, k, result_dev, per_vertex_dev, (cudaStream_t)stream);
+    // per-vertex counts: from the traversal the call names, except for
+    // k <= 2 (closed forms in the pivoting path) and sizes the orientation
+    // traversal does not take
+    if (pivot || (per_vertex_dev && !orient_per_vertex(g, k)))
+        return count_pivot_async(g, k, result_dev, per_vertex_dev, (cudaStream_t)stream);
+    a.per_vertex_dev = per_vertex_dev;
     return count_launch(g, a, result_dev, (cudaStream_t)stream);
 }
 
@@ -262,9 +271,8 @@ static kc_status count_sync(kc_graph* g, uint32_t k, int pivot, int scheme, uint
     if (!lo_out) return set_error(KC_E_INVALID_ARG, "total_out is NULL");
     CountArgs a;
     KC_CHECK(resolve(g, k, pivot, scheme, subwarp, a));
-    // per-vertex counts always come from the pivoting traversal restricted
-    // to size k (the same exact counts)
-    if (per_vertex_out) pivot = 1;
+    // per-vertex counts: as in kc_count_async
+    if (per_vertex_out && !orient_per_vertex(g, k)) pivot = 1;
     cudaStream_t s = (cudaStream_t)stream;
     KC_CHECK(dev_alloc(g->result, sizeof(kc_result) + 64));
     kc_result* rd = (kc_result*)g->result.ptr;
@@ -278,8 +286,12 @@ static kc_status count_sync(kc_graph* g, uint32_t k, int pivot, int scheme, uint
             pv_dev = per_vertex_out;
         }
     }
-    if (pivot) KC_CHECK(count_pivot_async(g, k, rd, pv_dev, s));
-    else KC_CHECK(count_launch(g, a, rd, s));
+    if (pivot) {
+        KC_CHECK(count_pivot_async(g, k, rd, pv_dev, s));
+    } else {
+        a.per_vertex_dev = pv_dev;
+        KC_CHECK(count_launch(g, a, rd, s));
+    }
     kc_result r;
     KC_CUDA(cudaMemcpyAsync(&r, rd, sizeof(r), cudaMemcpyDeviceToHost, s));
     if (pv_host && g->n) KC_CUDA(cudaMemcpyAsync(per_vertex_out, pv_dev, (size_t)g->n * 8, cudaMemcpyDeviceToHost, s));
@@ -288,6 +300,13 @@ static kc_status count_sync(kc_graph* g, uint32_t k, int pivot, int scheme, uint
     *lo_out = r.total;
     if (hi_out) *hi_out = r.total_hi;
     if (flags_out) *flags_out = r.flags;
+    if (r.status == KC_E_INTERNAL && g->ctl.ptr) {
+        // the first failed device-side check, if one was recorded
+        Ctl hc;
+        KC_CUDA(cudaMemcpy(&hc, g->ctl.ptr, sizeof(Ctl), cudaMemcpyDeviceToHost));
+        return set_error(KC_E_INTERNAL, "device reported KC_E_INTERNAL (check %u refused index %u)", hc.dbg_code,
+                         hc.dbg_idx);
+    }
     if (r.status != KC_OK) return set_error((kc_status)r.status, "device reported %s", kc_status_name(r.status));
     if (r.flags & (KC_FLAG_TOTAL_OVERFLOW | KC_FLAG_VERTEX_OVERFLOW))
         return set_error(KC_E_OVERFLOW, "a count exceeded 2^64 - 1");

@@ -61,6 +61,8 @@ struct Ctl {
     unsigned int work_next_aux;    // spare counter
     unsigned int bar_count;        // grid barrier arrivals
     unsigned int bar_gen;          // grid barrier generation
+    unsigned int dbg_code;         // first failed device-side bounds check (0 = none)
+    unsigned int dbg_idx;          // the index it refused
 };
 
 }  // namespace kc
@@ -182,15 +184,19 @@ kc_status batch_launch(const QDesc* q_dev, uint32_t nq, uint32_t d_cap, uint32_t
 // take).
 size_t batch_smem_bytes(uint32_t d_cap, uint32_t k_max, const BatchConfig& cfg);
 
-// kc_deep.cu: orientation-mode counts for k >= 5 with re-encoded small nodes.
+// kc_deep.cu: orientation-mode counts with re-encoded small nodes, for
+// k >= 5, and with per-vertex counts (pv) for k >= 3.
 // deep_supported: whether the kernel takes (graph, k).  deep_plan: global
 // scratch words and grid size of its launch.  deep_launch: enqueue it over
 // roots[0, n_work) (roots[0, n_big) with more than 32 candidates); task_next
-// and task_total hold n_big zeroed words each.
-bool deep_supported(const kc_graph* g, uint32_t k);
-kc_status deep_plan(const kc_graph* g, uint32_t k, bool ec, size_t* scratch_words, int* blocks_out);
+// and task_total hold n_big zeroed words each; pv (nullable): zeroed u64[n]
+// per-vertex accumulators in the library numbering.  pv_to_input: copy them
+// to out[n] in the input numbering.
+bool deep_supported(const kc_graph* g, uint32_t k, bool pv);
+kc_status deep_plan(const kc_graph* g, uint32_t k, bool ec, bool pv, size_t* scratch_words, int* blocks_out);
 kc_status deep_launch(kc_graph* g, uint32_t k, bool ec, uint32_t n_big, uint32_t n_work, uint32_t* task_next,
-                      uint32_t* task_total, uint32_t* gscratch, Ctl* ctl, cudaStream_t s);
+                      uint32_t* task_total, uint32_t* gscratch, unsigned long long* pv, Ctl* ctl, cudaStream_t s);
+kc_status pv_to_input(const kc_graph* g, const unsigned long long* pv, uint64_t* out, cudaStream_t s);
 
 // kc_pivot.cu
 // Fixed-k pivoting count into result_dev (device); per_vertex_dev: n entries
@@ -224,6 +230,16 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+
+// A device-side bounds check: false (and the first failure recorded in
+// c->dbg_code / dbg_idx, with KC_FLAG_INTERNAL) when idx >= bound; the
+// caller then skips the access.
+__device__ __forceinline__ bool in_bounds(Ctl* c, unsigned long long idx, unsigned long long bound, unsigned code) {
+    if (idx < bound) return true;
+    if (atomicCAS(&c->dbg_code, 0u, code) == 0u) c->dbg_idx = (unsigned)idx;
+    atomicOr(&c->flags, (unsigned)KC_FLAG_INTERNAL);
+    return false;
 }
 
 // Exact 128-bit accumulation of a 64-bit partial into (lo, hi).

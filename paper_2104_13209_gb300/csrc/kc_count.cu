@@ -625,8 +625,8 @@ static kc_status plan_launch(kc_graph* g, uint32_t k, uint32_t G, bool ec, Geome
 
 kc_status count_reserve(kc_graph* g, uint32_t k_max, int pivot, int per_vertex, cudaStream_t s) {
     (void)pivot;
-    (void)per_vertex;
     (void)s;
+    if (per_vertex) KC_CHECK(dev_alloc(g->pv, ((size_t)g->n + 16) * 8));
     KC_CHECK(dev_alloc(g->ctl, ctl_bytes()));
     size_t need = 64;
     for (uint32_t G : {1u, 2u, 4u, 8u, 16u, 32u})
@@ -637,11 +637,12 @@ kc_status count_reserve(kc_graph* g, uint32_t k_max, int pivot, int per_vertex, 
                 CountKernel kern;
                 KC_CHECK(plan_launch(g, k, G, ec != 0, geo, blocks, kern));
                 need = std::max(need, geo.gscratch_words * blocks + 64);
-                if (deep_supported(g, k)) {
-                    size_t sw = 0;
-                    KC_CHECK(deep_plan(g, k, ec != 0, &sw, &blocks));
-                    need = std::max(need, sw + 64);
-                }
+                for (int pv = 0; pv < 2; ++pv)
+                    if (deep_supported(g, k, pv != 0) && (pv == 0 || per_vertex)) {
+                        size_t sw = 0;
+                        KC_CHECK(deep_plan(g, k, ec != 0, pv != 0, &sw, &blocks));
+                        need = std::max(need, sw + 64);
+                    }
             }
     KC_CHECK(dev_alloc(g->scratch, need * 4));
     KC_CHECK(dev_alloc(g->tmp, (2 * (size_t)g->n + 64) * 4));
@@ -668,13 +669,22 @@ kc_status count_launch(kc_graph* g, const CountArgs& a, kc_result* result_dev, c
     const uint64_t n_work = roots_with_outdeg_at_least(g, k - 1);
     const uint64_t n_big = roots_with_outdeg_at_least(g, std::max<uint64_t>(SMALL_D + 1, k - 1));
     unsigned long long budget = g->time_limit_s > 0 ? (unsigned long long)(g->time_limit_s * 1e9) : 0ull;
-    if (deep_supported(g, k)) {
-        // k >= 5: the traversal with re-encoded small nodes (kc_deep.cu)
+    const bool pv = a.per_vertex_dev != nullptr;
+    if (pv && !deep_supported(g, k, true))
+        return set_error(KC_E_UNSUPPORTED, "per-vertex counts in orientation mode need 3 <= k <= 36");
+    if (deep_supported(g, k, pv)) {
+        // k >= 5, or per-vertex counts: the traversal with re-encoded small nodes (kc_deep.cu)
         size_t sw = 0;
         int dblocks = 0;
-        KC_CHECK(deep_plan(g, k, ec, &sw, &dblocks));
+        KC_CHECK(deep_plan(g, k, ec && !(pv && k < 4), pv, &sw, &dblocks));
         KC_CHECK(dev_alloc(g->scratch, (sw + 64) * 4));
         KC_CHECK(dev_alloc(g->tmp, (2 * (size_t)g->n + 64) * 4));
+        unsigned long long* pvacc = nullptr;
+        if (pv) {
+            KC_CHECK(dev_alloc(g->pv, ((size_t)g->n + 16) * 8));
+            pvacc = (unsigned long long*)g->pv.ptr;
+            KC_CUDA(cudaMemsetAsync(pvacc, 0, (size_t)g->n * 8, s));
+        }
         uint32_t* task_next = (uint32_t*)g->tmp.ptr;
         uint32_t* task_total = task_next + n_big;
         if (n_big) KC_CUDA(cudaMemsetAsync(task_next, 0, (size_t)n_big * 8, s));
@@ -683,7 +693,8 @@ kc_status count_launch(kc_graph* g, const CountArgs& a, kc_result* result_dev, c
         KC_CUDA(cudaGetLastError());
         if (n_work > 0)
             KC_CHECK(deep_launch(g, k, ec, (uint32_t)n_big, (uint32_t)n_work, task_next, task_total,
-                                 (uint32_t*)g->scratch.ptr, ctl, s));
+                                 (uint32_t*)g->scratch.ptr, pvacc, ctl, s));
+        if (pv) KC_CHECK(pv_to_input(g, pvacc, a.per_vertex_dev, s));
         k_finalize<<<1, 1, 0, s>>>(ctl, result_dev);
         note_launch();
         KC_CUDA(cudaGetLastError());

@@ -55,7 +55,52 @@ struct DeepParams {
     uint32_t wp;                 // words per bitmap row (a multiple of 4)
     uint32_t wide_levels;        // wide stack levels per warp
     uint32_t* task_total;        // per big root: its number of tasks (EC: edges of its sub-graph), 0 = unknown
+    unsigned long long* pv;      // per-vertex counts, library numbering (per-vertex variant)
+    uint32_t n;                  // vertices
 };
+
+// Per-vertex counts (PV).  A vertex gains, for every counted clique that
+// holds it, one: the root gains its tree's count, a vertex on the path to a
+// node gains the count of the node's subtree, and below a node whose last
+// two vertices are chosen together (the edges of the sub-graph induced by
+// L) a member j of L gains its degree in that sub-graph, popc(L & row_j) +
+// popc(L & column_j), read from the encoding and its transpose.
+struct PvCtx {
+    unsigned long long* pvc;  // block: per root candidate position, [d] = the root
+    const uint32_t* bmT;      // transposed root bitmap (row j = the candidates with j in their row)
+    uint32_t* TT;             // warp: transposed re-encoded rows
+    unsigned long long* pvm;  // warp: gains of the re-encoded members
+    uint32_t* scand;          // warp: a small root's candidates
+    uint32_t ncand;           // the current root's candidates (pvc has ncand + 1 entries)
+};
+
+// Per-warp shared memory of the per-vertex variant (after the wide stacks).
+struct DeepWarpPv {
+    uint32_t TT[CMAX * 4];
+    unsigned long long pvm[CMAX];
+    uint32_t scand[32];
+};
+static_assert(sizeof(DeepWarpPv) % 16 == 0, "per-warp areas keep 16-byte alignment");
+
+__device__ __forceinline__ void pv_add(unsigned long long* p, unsigned long long x, const Ctl* ctl) {
+    if (x == 0) return;
+    const unsigned long long old = atomicAdd(p, x);
+    if (old + x < old) atomicOr((unsigned*)&ctl->flags, (unsigned)KC_FLAG_VERTEX_OVERFLOW);
+}
+
+// pv_add to entry idx of an array of `bound` entries (bounds-checked)
+__device__ __forceinline__ void pv_add_at(unsigned long long* base, uint32_t idx, uint32_t bound, unsigned long long x,
+                                          const Ctl* ctl, unsigned code) {
+    if (x == 0) return;
+    if (!in_bounds(const_cast<Ctl*>(ctl), idx, bound, code)) return;
+    pv_add(base + idx, x, ctl);
+}
+
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
 
 // ---------------------------------------------------------------------------
 // Lane-level walk over a re-encoded node of nw words per row (nw = 1, 2, 4)
@@ -105,85 +150,167 @@ __device__ __forceinline__ uint32_t mask_pop(Mask<NW>& a) {
     return NONE;
 }
 
-// Edges of the sub-graph induced by J (rows T, nw words each).
-template <int NW>
-__device__ __forceinline__ unsigned long long lane_edges(Mask<NW> J, const uint32_t* T, unsigned long long& words) {
+// Edges of the sub-graph induced by J (rows T, nw words each).  PV: each
+// member gains its degree in that sub-graph (out-neighbours from T, in-
+// neighbours from the transpose TT).
+template <int NW, bool PV>
+__device__ __forceinline__ unsigned long long lane_edges(Mask<NW> J, const uint32_t* T, const PvCtx& X, const Ctl* ctl,
+                                                         unsigned long long& words) {
+    const Mask<NW> J0 = J;
     unsigned long long s = 0;
     for (;;) {
         const uint32_t v = mask_pop<NW>(J);
         if (v == NONE) break;
-        s += mask_popc<NW>(mask_and<NW>(J, T + (size_t)v * NW));
+        const uint32_t out = mask_popc<NW>(mask_and<NW>(J, T + (size_t)v * NW));
+        s += out;
         words += NW;
+        if (PV) {
+            const uint32_t in = mask_popc<NW>(mask_and<NW>(J0, X.TT + (size_t)v * NW));
+            pv_add_at(X.pvm, v, CMAX, out + in, ctl, 201u);
+            words += NW;
+        }
     }
     return s;
 }
 
 // rem-cliques of the sub-graph induced by J0 (rem >= 3), one lane alone.
-template <int NW>
+// PV: the vertex chosen at each level gains the count of its subtree
+// (pending sums flushed when the level moves on).
+template <int NW, bool PV>
 __device__ unsigned long long lane_walk_nw(const Ctl* ctl, Mask<NW> J0, uint32_t rem0, const uint32_t* T,
-                                           unsigned long long& words) {
+                                           const PvCtx& X, unsigned long long& words) {
     Mask<NW> stk[LANE_DEPTH];
-    unsigned long long acc = 0;
+    uint32_t cv[PV ? LANE_DEPTH : 1];
+    unsigned long long pend[PV ? LANE_DEPTH : 1];
+    unsigned long long acc = 0, tot = 0;
     int l = 0;
     stk[0] = J0;
+    if (PV) pend[0] = 0;
     uint32_t steps = 0;
+    auto flush = [&](int lv) {
+        if (PV && pend[lv]) {
+            pv_add_at(X.pvm, cv[lv], CMAX, pend[lv], ctl, 202u);
+            if (lv > 0) pend[lv - 1] += pend[lv];
+            else tot += pend[lv];
+            pend[lv] = 0;
+        }
+    };
     for (;;) {
         Mask<NW>& J = stk[l];
         const uint32_t rem = rem0 - l;
         if (mask_popc<NW>(J) < rem) {
+            if (PV) flush(l);
             if (l == 0) break;
             --l;
             continue;
         }
         if ((++steps & 65535u) == 0 && timed_out(ctl)) break;
         const uint32_t v = mask_pop<NW>(J);
+        if (PV) {
+            flush(l);
+            cv[l] = v;
+        }
         const Mask<NW> C = mask_and<NW>(J, T + (size_t)v * NW);
         words += NW;
         const uint32_t c = mask_popc<NW>(C);
         const uint32_t need = rem - 1;
         if (c < need) continue;
-        if (need == 1) {
-            acc += c;
-        } else if (need == 2) {
-            acc += lane_edges<NW>(C, T, words);
+        if (need == 2) {
+            const unsigned long long e = lane_edges<NW, PV>(C, T, X, ctl, words);
+            acc += e;
+            if (PV) pend[l] += e;
         } else {
             stk[++l] = C;
+            if (PV) pend[l] = 0;
         }
     }
+    (void)tot;
     return acc;
 }
 
-// rem-cliques (rem >= 2) of the re-encoded sub-graph on m vertices held in
-// dw.T, by the 32 lanes of the warp.  rem == 2: lanes take rows; rem == 3:
-// lanes take rows and count each row's edges; rem == 4: lanes claim rows and
-// count the edges below each of their edges; rem >= 5: lanes claim the edges
-// (a, b) of the sub-graph one at a time and walk below a & b.
+// The transpose of the re-encoded rows (X.TT: row b = the members a < b with
+// b in row a) and cleared member gains, for the per-vertex variant.
 template <int NW>
-__device__ void warp_small(const Ctl* ctl, DeepWarp& dw, uint32_t m, uint32_t rem, Acc& acc) {
+__device__ __forceinline__ void transpose_small(const DeepWarp& dw, const PvCtx& X, uint32_t m) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t b = 0; b < m; ++b) {
+#pragma unroll
+        for (int c = 0; c < NW; ++c) {
+            const uint32_t a = (uint32_t)c * 32 + lane;
+            const bool bit = a < m && a < b && ((dw.T[a * NW + (b >> 5)] >> (b & 31)) & 1u);
+            const uint32_t w = __ballot_sync(0xffffffffu, bit);
+            if (lane == c) X.TT[b * NW + c] = w;
+        }
+    }
+    for (uint32_t a = lane; a < m; a += 32) X.pvm[a] = 0;
+    __syncwarp();
+}
+
+// rem-cliques (rem >= 2) of the re-encoded sub-graph on m vertices held in
+// dw.T, by the 32 lanes of the warp; returns this lane's share of the count
+// (also added to acc).  rem == 2: lanes take rows; rem == 3: lanes take rows
+// and count each row's edges; rem == 4: lanes claim rows and count the edges
+// below each of their edges; rem >= 5: lanes claim the edges (a, b) of the
+// sub-graph one at a time and walk below a & b.
+// PV: X.pvm[a] receives the number of counted cliques holding member a.
+template <int NW, bool PV>
+__device__ unsigned long long warp_small(const Ctl* ctl, DeepWarp& dw, const PvCtx& X, uint32_t m, uint32_t rem,
+                                         Acc& acc) {
     const int lane = threadIdx.x & 31;
     const uint32_t* T = dw.T;
+    if (PV) transpose_small<NW>(dw, X, m);
+    unsigned long long s = 0;
     if (rem <= 3) {
-        unsigned long long s = 0;
         for (uint32_t a = lane; a < m; a += 32) {
             Mask<NW> R;
 #pragma unroll
             for (int i = 0; i < NW; ++i) R.w[i] = T[a * NW + i];
             if (rem == 2) {
-                s += mask_popc<NW>(R);
+                const uint32_t out = mask_popc<NW>(R);
+                s += out;
                 acc.words += NW;
+                if (PV) {
+                    Mask<NW> C;
+#pragma unroll
+                    for (int i = 0; i < NW; ++i) C.w[i] = X.TT[a * NW + i];
+                    pv_add_at(X.pvm, a, CMAX, out + mask_popc<NW>(C), ctl, 203u);
+                }
             } else {
-                s += lane_edges<NW>(R, T, acc.words);
+                // triangles with a as the smallest member
+                Mask<NW> B = R;
+                unsigned long long t = 0;
+                for (;;) {
+                    const uint32_t b = mask_pop<NW>(B);
+                    if (b == NONE) break;
+                    t += mask_popc<NW>(mask_and<NW>(R, T + (size_t)b * NW));
+                    acc.words += NW;
+                }
+                s += t;
+                if (PV) {
+                    // ... plus those with a as the middle or the largest member
+                    Mask<NW> C;
+#pragma unroll
+                    for (int i = 0; i < NW; ++i) C.w[i] = X.TT[a * NW + i];
+                    Mask<NW> A = C;
+                    for (;;) {
+                        const uint32_t x = mask_pop<NW>(A);
+                        if (x == NONE) break;
+                        t += mask_popc<NW>(mask_and<NW>(R, T + (size_t)x * NW));
+                        t += mask_popc<NW>(mask_and<NW>(C, T + (size_t)x * NW));
+                        acc.words += 2 * NW;
+                    }
+                    pv_add_at(X.pvm, a, CMAX, t, ctl, 204u);
+                }
             }
         }
         acc.add(s);
         __syncwarp();
-        return;
+        return s;
     }
     if (rem == 4) {
         // lanes claim rows; below each edge (a, b) of a row, count the edges of a & b
         if (lane == 0) dw.next = 0;
         __syncwarp();
-        unsigned long long s = 0;
         for (;;) {
             const uint32_t a = atomicAdd(&dw.next, 1u);
             if (a >= m) break;
@@ -191,17 +318,24 @@ __device__ void warp_small(const Ctl* ctl, DeepWarp& dw, uint32_t m, uint32_t re
 #pragma unroll
             for (int i = 0; i < NW; ++i) R.w[i] = T[a * NW + i];
             Mask<NW> B = R;
+            unsigned long long sa = 0;
             for (;;) {
                 const uint32_t b = mask_pop<NW>(B);
                 if (b == NONE) break;
                 const Mask<NW> J = mask_and<NW>(R, T + (size_t)b * NW);
                 acc.words += NW;
-                if (mask_popc<NW>(J) >= 2) s += lane_edges<NW>(J, T, acc.words);
+                if (mask_popc<NW>(J) >= 2) {
+                    const unsigned long long e = lane_edges<NW, PV>(J, T, X, ctl, acc.words);
+                    sa += e;
+                    if (PV) pv_add_at(X.pvm, b, CMAX, e, ctl, 205u);
+                }
             }
+            s += sa;
+            if (PV) pv_add_at(X.pvm, a, CMAX, sa, ctl, 206u);
         }
         acc.add(s);
         __syncwarp();
-        return;
+        return s;
     }
     // rem >= 5: edge tasks, numbered row by row
     uint32_t carry = 0;
@@ -228,7 +362,6 @@ __device__ void warp_small(const Ctl* ctl, DeepWarp& dw, uint32_t m, uint32_t re
     __syncwarp();
     const uint32_t total = carry;
     const uint32_t rem2 = rem - 2;  // vertices still to choose below an edge task
-    unsigned long long s = 0;
     for (;;) {
         const uint32_t t = atomicAdd(&dw.next, 1u);
         if (t >= total) break;
@@ -255,12 +388,19 @@ __device__ void warp_small(const Ctl* ctl, DeepWarp& dw, uint32_t m, uint32_t re
         acc.words += NW;
         const uint32_t c = mask_popc<NW>(J);
         if (c < rem2) continue;
-        if (rem2 == 1) s += c;
-        else if (rem2 == 2) s += lane_edges<NW>(J, T, acc.words);
-        else s += lane_walk_nw<NW>(ctl, J, rem2, T, acc.words);
+        unsigned long long e;
+        if (rem2 == 1) e = c;
+        else if (rem2 == 2) e = lane_edges<NW, PV>(J, T, X, ctl, acc.words);
+        else e = lane_walk_nw<NW, PV>(ctl, J, rem2, T, X, acc.words);
+        s += e;
+        if (PV) {
+            pv_add_at(X.pvm, lo, CMAX, e, ctl, 207u);
+            pv_add_at(X.pvm, b, CMAX, e, ctl, 208u);
+        }
     }
     acc.add(s);
     __syncwarp();
+    return s;
 }
 
 // ---------------------------------------------------------------------------
@@ -282,6 +422,7 @@ __device__ __forceinline__ void list_members(const uint32_t* L, uint32_t wp, Dee
             if (lane >= o) incl += y;
         }
         uint32_t o = carry + incl - c;
+        if (x < wp && wp <= CMAX + 4) dw.pre[x] = o;  // word prefix, for reencode_rows
         uint32_t bits = bits0;
         while (bits) {
             if (o < CMAX) dw.pos[o] = (uint16_t)((x << 5) + (__ffs(bits) - 1));
@@ -293,8 +434,48 @@ __device__ __forceinline__ void list_members(const uint32_t* L, uint32_t wp, Dee
     __syncwarp();
 }
 
+// Re-encode the sub-graph induced by L (m <= CMAX members, word prefixes of L
+// in dw.pre, wp <= CMAX + 4) into dw.T with NW words per row, one lane per
+// row: each member of row pos[a] & L at word x and bit i becomes bit
+// pre[x] + popc(L[x] below i) of row a.  The work follows the sub-graph's
+// edges, not m^2.
+template <int NW>
+__device__ __forceinline__ void reencode_rows(const uint32_t* bm, const uint32_t* L, uint32_t wp, uint32_t m,
+                                              DeepWarp& dw) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t a = lane; a < m; a += 32) {
+        const uint32_t pa = dw.pos[a];
+        const uint32_t* row = bm + (size_t)pa * wp;
+        uint32_t o0 = 0, o1 = 0, o2 = 0, o3 = 0;
+        for (uint32_t x = pa >> 5; x < wp; ++x) {
+            const uint32_t lx = L[x];
+            uint32_t v = row[x] & lx;
+            if (!v) continue;
+            const uint32_t base = dw.pre[x];
+            while (v) {
+                const uint32_t i = __ffs(v) - 1;
+                v &= v - 1;
+                const uint32_t idx = base + __popc(lx & ((1u << i) - 1u));
+                const uint32_t bit = 1u << (idx & 31);
+                if (idx < 32) o0 |= bit;
+                else if (idx < 64) o1 |= bit;
+                else if (idx < 96) o2 |= bit;
+                else o3 |= bit;
+            }
+        }
+        dw.T[a * NW] = o0;
+        if (NW > 1) dw.T[a * NW + 1 % NW] = o1;
+        if (NW > 2) {
+            dw.T[a * NW + 2 % NW] = o2;
+            dw.T[a * NW + 3 % NW] = o3;
+        }
+    }
+    __syncwarp();
+}
+
 // Re-encode the sub-graph induced by L (m <= CMAX members) into dw.T with NW
-// words per row: bit b of row a iff pos[b] is in row pos[a] of bm.
+// words per row: bit b of row a iff pos[b] is in row pos[a] of bm (32 bits
+// at a time by warp ballots; for rows too wide for reencode_rows).
 template <int NW>
 __device__ __forceinline__ void reencode(const uint32_t* bm, uint32_t wp, uint32_t m, DeepWarp& dw) {
     const int lane = threadIdx.x & 31;
@@ -318,13 +499,16 @@ __device__ __forceinline__ void reencode(const uint32_t* bm, uint32_t wp, uint32
 }
 
 // Edges of the sub-graph induced by L (rows of bm, wp words each): lanes take
-// the members (positions from a word prefix), each sums popc(L & row_j) from
-// j's word on.
+// the words of L round-robin, and for each member j in them sum
+// popc(L & row_j) from j's word on.  PV: j gains its degree in the sub-graph,
+// the in-neighbours read from the transposed bitmap (row j of bmT, words up
+// to j's).
+template <bool PV>
 __device__ __forceinline__ unsigned long long wide_edges(const uint32_t* L, const uint32_t* bm, uint32_t wp,
-                                                         uint32_t lo, unsigned long long& words) {
+                                                         uint32_t lo, const PvCtx& X, const Ctl* ctl,
+                                                         unsigned long long& words) {
     const int lane = threadIdx.x & 31;
     unsigned long long s = 0;
-    // lanes take words of L round-robin and the members in them
     for (uint32_t w = lo + lane; w < wp; w += 32) {
         uint32_t bits = L[w];
         while (bits) {
@@ -342,6 +526,50 @@ __device__ __forceinline__ unsigned long long wide_edges(const uint32_t* L, cons
             for (; x < wp; ++x) c += __popc(L[x] & rj[x]);
             s += c;
             words += wp - w;
+            if (PV) {
+                const uint32_t* tj = X.bmT + (size_t)j * wp;
+                uint32_t in = 0;
+                for (uint32_t y = lo; y <= w; ++y) in += __popc(L[y] & tj[y]);
+                words += w - lo + 1;
+                pv_add_at(X.pvc, j, X.ncand + 1, (unsigned long long)c + in, ctl, 209u);
+            }
+        }
+    }
+    return s;
+}
+
+// wide_edges for m <= CMAX members listed in dw.pos: the lanes take the
+// members, first and last alternately (row lengths fall with the position),
+// so every lane scans about the same number of words.
+template <bool PV>
+__device__ __forceinline__ unsigned long long wide_edges_listed(const uint32_t* L, const uint32_t* bm, uint32_t wp,
+                                                                uint32_t lo, uint32_t m, const DeepWarp& dw,
+                                                                const PvCtx& X, const Ctl* ctl,
+                                                                unsigned long long& words) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long s = 0;
+    for (uint32_t i = lane; i < m; i += 32) {
+        const uint32_t jj = (i & 1u) ? m - 1 - (i >> 1) : (i >> 1);
+        const uint32_t j = dw.pos[jj];
+        const uint32_t w = j >> 5;
+        const uint32_t* rj = bm + (size_t)j * wp;
+        uint32_t c = 0;
+        uint32_t x = w;
+        for (; x < wp && (x & 3u) != 0; ++x) c += __popc(L[x] & rj[x]);
+        for (; x + 4 <= wp; x += 4) {
+            const uint4 a = *reinterpret_cast<const uint4*>(L + x);
+            const uint4 r = *reinterpret_cast<const uint4*>(rj + x);
+            c += __popc(a.x & r.x) + __popc(a.y & r.y) + __popc(a.z & r.z) + __popc(a.w & r.w);
+        }
+        for (; x < wp; ++x) c += __popc(L[x] & rj[x]);
+        s += c;
+        words += wp - w;
+        if (PV) {
+            const uint32_t* tj = X.bmT + (size_t)j * wp;
+            uint32_t in = 0;
+            for (uint32_t y = lo; y <= w; ++y) in += __popc(L[y] & tj[y]);
+            words += w - lo + 1;
+            pv_add_at(X.pvc, j, X.ncand + 1, (unsigned long long)c + in, ctl, 209u);
         }
     }
     return s;
@@ -357,76 +585,270 @@ __device__ __forceinline__ uint32_t warp_popc(const uint32_t* L, uint32_t lo, ui
     return c;
 }
 
-// The node (L, rem) of the root's tree: L has m members (m >= rem), its
-// words below lo are zero.  stk: the warp's wide stack (levels x wp words).
-__device__ void deep_node(const DeepParams& D, const uint32_t* bm, const uint32_t* L0, uint32_t lo0, uint32_t m0,
-                          uint32_t rem0, uint32_t* stk, DeepWarp& dw, Acc& acc) {
+// ---------------------------------------------------------------------------
+// Sharing the wide levels between the warps of a block.  A root's giant
+// subtrees (hubs of a dense core) would otherwise run on one warp while the
+// block's other warps wait.  A warp walking a wide level donates the upper
+// half of the remaining children of its shallowest splittable level when
+// warps are idle: the frame holds a copy of the level's list, the cursor
+// and end of the donated range, the members from the cursor on (for the size
+// bound), the number of vertices still to choose, and (per-vertex counts)
+// the path positions whose gains include the frame's count.
+// ---------------------------------------------------------------------------
+static constexpr int DQCAP = 8;
+static constexpr int DPATH = LANE_DEPTH + 4;
+// A warp waiting for a frame gives up after this long (the donors finish
+// their own work, so leaving is always safe).
+static constexpr unsigned long long DEEP_IDLE_NS = 2000000000ull;
+
+struct DeepSteal {
+    unsigned idle;     // warps waiting for a frame (or trying to take one)
+    unsigned active;   // warps still in the session
+    unsigned queued;   // frames ready
+    unsigned left_pool;  // warps that stopped waiting after DEEP_IDLE_NS
+    unsigned state[DQCAP];  // 0 empty, 1 being written, 2 ready, 3 being read
+    unsigned meta[DQCAP][4];  // cursor, end, rem, members after the cursor
+    unsigned npath[DQCAP];
+    unsigned path[DQCAP][DPATH];
+};
+
+// Lane-indexed warp-uniform array: lane i holds entry i.
+__device__ __forceinline__ uint32_t lget(uint32_t reg, int i) { return __shfl_sync(0xffffffffu, reg, i); }
+__device__ __forceinline__ unsigned long long lget64(unsigned long long reg, int i) {
+    return __shfl_sync(0xffffffffu, reg, i);
+}
+
+// members of L in (a, b) (positions), over the warp
+__device__ __forceinline__ uint32_t warp_range_popc(const uint32_t* L, uint32_t a, uint32_t b, uint32_t wp) {
+    const int lane = threadIdx.x & 31;
+    uint32_t c = 0;
+    const uint32_t lo = a + 1;  // a = NONE wraps to 0
+    if (lo < b) {
+        const uint32_t w0 = lo >> 5, w1 = min((b - 1) >> 5, wp - 1);
+        for (uint32_t w = w0 + lane; w <= w1; w += 32) {
+            uint32_t x = L[w];
+            if (w == w0) x &= 0xFFFFFFFFu << (lo & 31);
+            if (w == ((b - 1) >> 5)) x &= 0xFFFFFFFFu >> (31 - ((b - 1) & 31));
+            c += __popc(x);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    return c;
+}
+
+// Where a walk starts: either a node (L, lo, m, rem) to analyse, or a donated
+// frame (a level with list L whose children after `cursor` and before `end`
+// remain; `cnt` members after the cursor; rem for the level's node).
+struct WalkStart {
+    const uint32_t* L;
+    uint32_t lo, m, rem;
+    bool frame;
+    uint32_t cursor, end, cnt;
+};
+
+// The walk of the root's tree from s.  stk: the warp's wide stack (levels x
+// wp words).  path / npath: positions (among the root's candidates) on the
+// path above s, warp-uniform (lane i holds entry i); with PV every count
+// below s is also their gain (the root's gain is added by the caller).
+// PV: returns the count below s (the same on every lane); the members of the
+// nodes below and the vertices chosen at the wide levels gain theirs.
+template <bool PV>
+__device__ unsigned long long deep_walk(const DeepParams& D, const uint32_t* bm, const WalkStart& s0, uint32_t* stk,
+                                        DeepWarp& dw, const PvCtx& X, Acc& acc, DeepSteal* ss, uint32_t* qwords,
+                                        uint32_t path_reg, uint32_t npath) {
     const int lane = threadIdx.x & 31;
     const uint32_t wp = D.wp;
     const Ctl* ctl = D.base.ctl;
-    // explicit stack of wide levels: list, cursor, members left above the cursor
-    uint32_t cur[LANE_DEPTH], left[LANE_DEPTH];
-    const uint32_t* Ls[LANE_DEPTH];
+    // wide levels, lane-indexed: cursor, end of the range, members after the
+    // cursor, pending count (PV); level l's list is Ls0 (l = 0) or stk + (l - 1) wp
+    uint32_t cur_r = 0, end_r = 0, left_r = 0;
+    unsigned long long pend_r = 0;
+    const uint32_t* Ls0 = s0.L;
+    unsigned long long tot = 0;
     int l = -1;
-    const uint32_t* L = L0;
-    uint32_t lo = lo0, m = m0, rem = rem0;
+    const uint32_t rem0 = s0.rem;
+    const uint32_t* L = s0.L;
+    uint32_t lo = s0.lo, m = s0.m, rem = s0.rem;
     uint32_t steps = 0;
+    bool analyse = !s0.frame;
+    if (s0.frame) {
+        l = 0;
+        if (lane == 0) {
+            cur_r = s0.cursor;
+            end_r = s0.end;
+            left_r = s0.cnt;
+            pend_r = 0;
+        }
+    }
+    auto lst = [&](int lv) -> const uint32_t* { return lv == 0 ? Ls0 : stk + (size_t)(lv - 1) * wp; };
+    // PV: the vertex chosen at level lv gains its subtree; so do the levels above
+    auto flush = [&](int lv) {
+        if (!PV) return;
+        const unsigned long long p = lget64(pend_r, lv);
+        if (p == 0) return;
+        const uint32_t cv = lget(cur_r, lv);  // every lane takes part in the shuffle
+        if (lane == 0) pv_add_at(X.pvc, cv, X.ncand + 1, p, ctl, 212u);
+        if (lv > 0) {
+            if (lane == lv - 1) pend_r += p;
+        } else {
+            tot += p;
+        }
+        if (lane == lv) pend_r = 0;
+    };
     for (;;) {
-        // analyse the node (L, lo, m, rem)
-        bool descend = false;
-        if (rem == 1) {
-            if (lane == 0) acc.add(m);
-        } else if (rem == 2) {
-            acc.add(wide_edges(L, bm, wp, lo, acc.words));
-        } else if (m <= CMAX) {
-            list_members(L, wp, dw);
-            if (m <= 32) {
-                reencode<1>(bm, wp, m, dw);
-                warp_small<1>(ctl, dw, m, rem, acc);
-            } else if (m <= 64) {
-                reencode<2>(bm, wp, m, dw);
-                warp_small<2>(ctl, dw, m, rem, acc);
-            } else {
-                reencode<4>(bm, wp, m, dw);
-                warp_small<4>(ctl, dw, m, rem, acc);
+        if (analyse) {
+            bool descend = false;
+            unsigned long long c_node = 0;  // PV: the node's count when it is finished here
+            if (rem == 1) {
+                if (lane == 0) acc.add(m);
+                c_node = m;
+                if (PV) {
+                    for (uint32_t w = lo + lane; w < wp; w += 32) {
+                        uint32_t bits = L[w];
+                        while (bits) {
+                            pv_add_at(X.pvc, (w << 5) + (__ffs(bits) - 1), X.ncand + 1, 1ull, ctl, 210u);
+                            bits &= bits - 1;
+                        }
+                    }
+                }
+            } else if (rem == 2) {
+                unsigned long long e;
+                if (m <= CMAX) {
+                    list_members(L, wp, dw);
+                    e = wide_edges_listed<PV>(L, bm, wp, lo, m, dw, X, ctl, acc.words);
+                    __syncwarp();
+                } else {
+                    e = wide_edges<PV>(L, bm, wp, lo, X, ctl, acc.words);
+                }
+                acc.add(e);
+                if (PV) c_node = warp_sum64(e);
+            } else if (m <= CMAX) {
+                list_members(L, wp, dw);
+                unsigned long long e;
+                const bool rows = wp <= CMAX + 4;
+                if (m <= 32) {
+                    if (rows) reencode_rows<1>(bm, L, wp, m, dw); else reencode<1>(bm, wp, m, dw);
+                    e = warp_small<1, PV>(ctl, dw, X, m, rem, acc);
+                } else if (m <= 64) {
+                    if (rows) reencode_rows<2>(bm, L, wp, m, dw); else reencode<2>(bm, wp, m, dw);
+                    e = warp_small<2, PV>(ctl, dw, X, m, rem, acc);
+                } else {
+                    if (rows) reencode_rows<4>(bm, L, wp, m, dw); else reencode<4>(bm, wp, m, dw);
+                    e = warp_small<4, PV>(ctl, dw, X, m, rem, acc);
+                }
+                if (PV) {
+                    c_node = warp_sum64(e);
+                    for (uint32_t a = lane; a < m; a += 32) pv_add_at(X.pvc, dw.pos[a], X.ncand + 1, X.pvm[a], ctl, 211u);
+                    __syncwarp();
+                }
+            } else if (l + 1 < (int)D.wide_levels && l + 1 < LANE_DEPTH) {
+                descend = true;
+            } else if (lane == 0) {
+                atomicOr((unsigned*)&ctl->flags, (unsigned)KC_FLAG_INTERNAL);  // cannot happen: depth < k
             }
-        } else if (l + 1 < (int)D.wide_levels && l + 1 < LANE_DEPTH) {
-            descend = true;
-        } else if (lane == 0) {
-            atomicOr((unsigned*)&ctl->flags, (unsigned)KC_FLAG_INTERNAL);  // cannot happen: depth < k
+            if (PV && !descend) {
+                if (l >= 0) {
+                    if (lane == l) pend_r += c_node;
+                } else {
+                    tot += c_node;
+                }
+            }
+            if (descend) {
+                ++l;
+                if (l == 0) Ls0 = L;
+                if (lane == l) {
+                    cur_r = lo * 32 - 1;  // before the first member (NONE when lo == 0)
+                    end_r = NONE;
+                    left_r = m;
+                    pend_r = 0;
+                }
+            }
         }
-        if (descend) {
-            ++l;
-            Ls[l] = L;
-            cur[l] = lo * 32 - 1;  // before the first member (NONE when lo == 0; next_bit starts at cur + 1)
-            left[l] = m;
-        }
+        analyse = true;
         // next child of the deepest wide level that still has one
         for (;;) {
-            if (l < 0) return;
+            if (l < 0) return tot;
             const uint32_t r = rem0 - (uint32_t)l;  // rem of level l's node
-            if (left[l] < r) {
+            if (lget(left_r, l) < r) {
+                flush(l);
                 --l;
                 continue;
             }
-            if ((++steps & 1023u) == 0) {
-                int to = lane == 0 ? (int)timed_out(ctl) : 0;
-                if (__shfl_sync(0xffffffffu, to, 0)) return;
+            if ((++steps & 63u) == 0) {
+                if ((steps & 1023u) == 0) {
+                    int to = lane == 0 ? (int)timed_out(ctl) : 0;
+                    if (__shfl_sync(0xffffffffu, to, 0)) return tot;
+                }
+                // donate the upper half of the shallowest level with two or more children left
+                int want = 0;
+                if (lane == 0) want = *(volatile unsigned*)&ss->idle > 0 && *(volatile unsigned*)&ss->queued < DQCAP;
+                if (__shfl_sync(0xffffffffu, want, 0)) {
+                    for (int lv = 0; lv <= l; ++lv) {
+                        const uint32_t* Lv = lst(lv);
+                        const uint32_t cv = lget(cur_r, lv), ev = lget(end_r, lv);
+                        const uint32_t nr = warp_range_popc(Lv, cv, ev, wp);
+                        if (nr < 2 || lget(left_r, lv) < rem0 - (uint32_t)lv) continue;
+                        uint32_t q = NONE, split = NONE;
+                        if (lane == 0) {
+                            split = select_above(Lv, cv, nr / 2, wp);
+                            for (uint32_t x = 0; x < DQCAP; ++x)
+                                if (*(volatile unsigned*)&ss->state[x] == 0 && atomicCAS(&ss->state[x], 0u, 1u) == 0u) {
+                                    q = x;
+                                    break;
+                                }
+                        }
+                        q = __shfl_sync(0xffffffffu, q, 0);
+                        split = __shfl_sync(0xffffffffu, split, 0);
+                        if (q == NONE || split == NONE) break;
+                        uint32_t* dst = qwords + (size_t)q * wp;
+                        for (uint32_t w = lane; w < wp; w += 32) dst[w] = Lv[w];
+                        const uint32_t tc = warp_range_popc(Lv, split - 1, NONE, wp);
+                        // path of the donated children: the path above this walk, then the
+                        // vertices chosen at levels 0 .. lv - 1
+                        const uint32_t np = npath + (uint32_t)lv;
+                        if (PV) {
+                            if (lane < (int)npath) ss->path[q][lane] = path_reg;
+                            const uint32_t cr = cur_r;  // lane i: level i's vertex
+                            if (lane < lv) ss->path[q][npath + lane] = cr;
+                        }
+                        if (lane == 0) {
+                            ss->meta[q][0] = split - 1;
+                            ss->meta[q][1] = ev;
+                            ss->meta[q][2] = rem0 - (uint32_t)lv;
+                            ss->meta[q][3] = tc;
+                            ss->npath[q] = np;
+                        }
+                        __syncwarp();
+                        if (lane == 0) {
+                            __threadfence_block();
+                            atomicExch(&ss->state[q], 2u);
+                            atomicAdd(&ss->queued, 1u);
+                        }
+                        if (lane == lv) end_r = split;
+                        break;
+                    }
+                }
             }
-            const uint32_t v = next_bit(Ls[l], cur[l] + 1, wp - 1);  // cur = NONE wraps to 0
+            const uint32_t* Ll = lst(l);
+            uint32_t v = next_bit(Ll, lget(cur_r, l) + 1, wp - 1);  // cur = NONE wraps to 0
+            if (v != NONE && v >= lget(end_r, l)) v = NONE;
+            flush(l);
             if (v == NONE) {
                 --l;
                 continue;
             }
-            cur[l] = v;
-            --left[l];
+            if (lane == l) {
+                cur_r = v;
+                --left_r;
+            }
             uint32_t* C = stk + (size_t)l * wp;
             const uint32_t clo = (v + 1) >> 5;
             const uint32_t* rv = bm + (size_t)v * wp;
             __syncwarp();
             uint32_t c = 0;
             for (uint32_t w = lane; w < wp; w += 32) {
-                const uint32_t x = w >= clo ? (Ls[l][w] & rv[w]) : 0u;
+                const uint32_t x = w >= clo ? (Ll[w] & rv[w]) : 0u;
                 C[w] = x;
                 c += __popc(x);
             }
@@ -442,6 +864,70 @@ __device__ void deep_node(const DeepParams& D, const uint32_t* bm, const uint32_
             break;
         }
     }
+}
+
+// A warp out of tasks: take a donated frame (copied to own, wp words; meta
+// and path to *f), or wait until one appears or every warp of the block is
+// idle.  Returns false when the session is over for this warp.
+__device__ bool deep_steal(const Ctl* ctl, DeepSteal* ss, const uint32_t* qwords, uint32_t wp, uint32_t* own,
+                           WalkStart* f, uint32_t* path_reg, uint32_t* npath) {
+    const int lane = threadIdx.x & 31;
+    uint32_t q = NONE;
+    if (lane == 0) {
+        atomicAdd(&ss->idle, 1u);
+        const unsigned long long t0 = globaltimer_ns();
+        bool done = false;
+        for (uint32_t it = 0;; ++it) {
+            if (*(volatile unsigned*)&ss->queued > 0) {
+                atomicSub(&ss->idle, 1u);  // trying to take work: no longer idle
+                for (uint32_t x = 0; x < DQCAP; ++x)
+                    if (*(volatile unsigned*)&ss->state[x] == 2u && atomicCAS(&ss->state[x], 2u, 3u) == 2u) {
+                        q = x;
+                        break;
+                    }
+                if (q != NONE) {
+                    atomicSub(&ss->queued, 1u);
+                    break;
+                }
+                atomicAdd(&ss->idle, 1u);
+            }
+            if (*(volatile unsigned*)&ss->idle == *(volatile unsigned*)&ss->active &&
+                *(volatile unsigned*)&ss->queued == 0) {
+                done = true;
+                break;
+            }
+            if ((it & 255u) == 255u) {
+                if (timed_out(ctl) || globaltimer_ns() - t0 > DEEP_IDLE_NS) {
+                    // leave the pool: the warps still walking finish their own frames
+                    atomicSub(&ss->idle, 1u);
+                    atomicSub(&ss->active, 1u);
+                    atomicAdd(&ss->left_pool, 1u);
+                    done = true;
+                    break;
+                }
+            }
+            __nanosleep(128);
+        }
+        (void)done;
+    }
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (q == NONE) return false;
+    __threadfence_block();
+    const uint32_t* src = qwords + (size_t)q * wp;
+    for (uint32_t w = lane; w < wp; w += 32) own[w] = src[w];
+    f->L = own;
+    f->frame = true;
+    f->cursor = ss->meta[q][0];
+    f->end = ss->meta[q][1];
+    f->rem = ss->meta[q][2];
+    f->cnt = ss->meta[q][3];
+    f->lo = 0;
+    f->m = 0;
+    *npath = ss->npath[q];
+    *path_reg = lane < (int)*npath ? ss->path[q][lane] : 0u;
+    __syncwarp();
+    if (lane == 0) atomicExch(&ss->state[q], 0u);
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -474,31 +960,90 @@ __device__ uint32_t deep_next_slot(const DeepParams& D, WorkCtl* wc, int& phase)
     return NONE;
 }
 
-template <bool EC>
+// bmT = the transpose of the d x d bitmap bm (rows of wp words): tiles of
+// 32 x 32 bits, one per warp at a time, turned by ballots.
+__device__ void transpose_bitmap(const uint32_t* bm, uint32_t* bmT, uint32_t d, uint32_t wp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t x = threadIdx.x; x < d * wp; x += DBLOCK) bmT[x] = 0;
+    __syncthreads();
+    const uint32_t nt = (d + 31) >> 5;
+    for (uint32_t t = warp; t < nt * nt; t += DW) {
+        const uint32_t ti = t / nt, tj = t % nt;
+        if (tj < ti) continue;  // rows only have bits above the diagonal
+        const uint32_t r = ti * 32 + lane;
+        const uint32_t w = r < d ? bm[(size_t)r * wp + tj] : 0u;
+        uint32_t mine = 0;
+        for (int b = 0; b < 32; ++b) {
+            const uint32_t col = __ballot_sync(0xffffffffu, (w >> b) & 1u);
+            if (lane == b) mine = col;
+        }
+        const uint32_t c = tj * 32 + lane;
+        if (c < d) bmT[(size_t)c * wp + ti] = mine;
+    }
+    __syncthreads();
+}
+
+// Rows of a small root's induced sub-graph (at most 32 candidates) into
+// dw.T, one word per row, and its candidates into X.scand (one warp).
+__device__ __forceinline__ uint32_t small_root_rows(const CountParams& P, uint32_t u, DeepWarp& dw, const PvCtx& X) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t b0 = P.rp[u];
+    const uint32_t d = P.rp[u + 1] - b0;
+    if (lane < (int)d) X.scand[lane] = P.col[b0 + lane];
+    __syncwarp();
+    const uint32_t last = X.scand[d - 1];
+    uint32_t rb = 0, re = 0;
+    if (lane < (int)d) {
+        rb = __ldg(P.rp + X.scand[lane]);
+        re = __ldg(P.rp + X.scand[lane] + 1);
+    }
+    for (uint32_t r = 0; r < d; ++r) {
+        const uint32_t xb = __shfl_sync(0xffffffffu, rb, r), xe = __shfl_sync(0xffffffffu, re, r);
+        uint32_t bits = 0;
+        scan_row(P.col, xb, xe, last, lane, [&](uint32_t y) {
+            const uint32_t pos = find_sorted(X.scand, r + 1, d, y);
+            if (pos != NONE) bits |= 1u << pos;
+        });
+        bits = __reduce_or_sync(0xffffffffu, bits);
+        if (lane == 0) dw.T[r] = bits;
+    }
+    __syncwarp();
+    return d;
+}
+
+template <bool EC, bool PV>
 __global__ void __launch_bounds__(DBLOCK) k_count_deep(const DeepParams D) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ DeepShared sh;
+    __shared__ DeepSteal ss;
     const CountParams& P = D.base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t wp = D.wp;
     const uint32_t D0 = (P.dcap + 31) & ~31u;
-    // layout: candidates | task prefix (EC) | per-warp areas | hash table | bitmap | wide stacks
+    const size_t wstride = (size_t)(D.wide_levels + 1) * wp;         // wide stack words per warp
+    // layout: candidates | task prefix (EC) | per-warp areas | donated frames | hash table |
+    //         bitmap | wide stacks [PV: transposed bitmap | per-warp PV areas | per-candidate gains]
     uint32_t* cand = smem;
     uint32_t* tpre = cand + D0;                                      // D0 + 32 words
     DeepWarp* dws = reinterpret_cast<DeepWarp*>(tpre + D0 + 32);
-    uint16_t* tab = reinterpret_cast<uint16_t*>(dws + DW);
+    uint32_t* qwords = reinterpret_cast<uint32_t*>(dws + DW);        // DQCAP x wp words
+    uint16_t* tab = reinterpret_cast<uint16_t*>(qwords + (size_t)DQCAP * wp);
     uint32_t* after_tab = reinterpret_cast<uint32_t*>(tab) + P.hash_words;
-    uint32_t* bm;
-    uint32_t* wide;
-    if (P.in_smem) {
-        bm = after_tab;
-        wide = bm + (size_t)P.dcap * wp;
-    } else {
-        bm = P.gscratch + (size_t)blockIdx.x * P.gscratch_words;
-        wide = bm + (size_t)P.dcap * wp;
-    }
+    uint32_t* region = P.in_smem ? after_tab : P.gscratch + (size_t)blockIdx.x * P.gscratch_words;
+    uint32_t* bm = region;
+    uint32_t* wide = bm + (size_t)P.dcap * wp;
+    uint32_t* bmT = wide + (size_t)DW * wstride;                      // PV
+    uint32_t* pv_smem = P.in_smem ? bmT + (PV ? (size_t)P.dcap * wp : 0) : after_tab;
+    DeepWarpPv* pvw = reinterpret_cast<DeepWarpPv*>(pv_smem);         // PV
+    unsigned long long* pvc = reinterpret_cast<unsigned long long*>(pvw + DW);  // PV: D0 + 1 entries
     DeepWarp& dw = dws[warp];
-    uint32_t* stk = wide + (size_t)warp * D.wide_levels * wp;
+    uint32_t* stk = wide + (size_t)warp * wstride;
+    PvCtx X;
+    X.pvc = pvc;
+    X.bmT = bmT;
+    X.TT = pvw[warp].TT;
+    X.pvm = pvw[warp].pvm;
+    X.scand = pvw[warp].scand;
     Acc acc;
     WorkCtl* wc = reinterpret_cast<WorkCtl*>(P.ctl + 1);
     int phase = 0;
@@ -513,7 +1058,12 @@ __global__ void __launch_bounds__(DBLOCK) k_count_deep(const DeepParams D) {
         if (s == NONE) break;
         const uint32_t u = P.roots[s];
         const uint32_t d = load_root(P.rp, P.col, u, cand);
+        X.ncand = d;
         build_bitmap_hashed<DBLOCK>(P.rp, P.col, cand, d, wp, bm, tab, hash_bits_for(d));
+        if (PV) {
+            for (uint32_t i = threadIdx.x; i <= d; i += DBLOCK) pvc[i] = 0;
+            transpose_bitmap(bm, bmT, d, wp);
+        }
         // task count: VC the root's edges to its candidates, EC the edges of
         // its induced sub-graph (numbered row by row through tpre)
         if (EC) {
@@ -541,6 +1091,12 @@ __global__ void __launch_bounds__(DBLOCK) k_count_deep(const DeepParams D) {
         } else if (threadIdx.x == 0) {
             sh.total = d;
         }
+        if (threadIdx.x == 0) {
+            ss.idle = 0;
+            ss.active = DW;
+            ss.queued = 0;
+            for (int x = 0; x < DQCAP; ++x) ss.state[x] = 0;
+        }
         __syncthreads();
         const uint32_t total = sh.total;
         if (threadIdx.x == 0 && P.help_min && total) atomicMax(&D.task_total[s], total);
@@ -556,46 +1112,105 @@ __global__ void __launch_bounds__(DBLOCK) k_count_deep(const DeepParams D) {
             if (t0 >= total) break;
             const uint32_t t1 = min(t0 + chunk, total);
             for (uint32_t t = t0; t < t1; ++t) {
-            if (!EC) {
-                // root edge u -> cand[t]: the node row t, k - 2 vertices to choose
-                const uint32_t* R = bm + (size_t)t * wp;
-                const uint32_t lo = (t + 1) >> 5;
-                const uint32_t m = warp_popc(R, lo, wp);
-                if (m + 2 >= k) deep_node(D, bm, R, lo, m, k - 2, stk, dw, acc);
-            } else {
-                // root triangle (u, cand[a], cand[b]), b the r-th member of row a
-                uint32_t lo_ = 0, hi_ = d;
-                while (hi_ - lo_ > 1) {
-                    const uint32_t mid = (lo_ + hi_) >> 1;
-                    if (tpre[mid] <= t) lo_ = mid; else hi_ = mid;
-                }
-                const uint32_t a = lo_;
-                const uint32_t* Ra = bm + (size_t)a * wp;
-                const uint32_t b = select_above(Ra, a, t - tpre[a], wp);
-                // the node row a & row b (k - 3 to choose) in the warp's first stack level
-                uint32_t* C = stk;
-                const uint32_t lo = (b + 1) >> 5;
-                const uint32_t* Rb = bm + (size_t)b * wp;
-                uint32_t c = 0;
-                for (uint32_t w = lane; w < wp; w += 32) {
-                    const uint32_t x = w >= lo ? (Ra[w] & Rb[w]) : 0u;
-                    C[w] = x;
-                    c += __popc(x);
-                }
-                acc.words += (lane == 0) ? (wp - lo) : 0;
+                if (!EC) {
+                    // root edge u -> cand[t]: the node row t, k - 2 vertices to choose
+                    const uint32_t* R = bm + (size_t)t * wp;
+                    const uint32_t lo = (t + 1) >> 5;
+                    const uint32_t m = warp_popc(R, lo, wp);
+                    if (m + 2 >= k) {
+                        const WalkStart w0{R, lo, m, k - 2, false, 0u, 0u, 0u};
+                        const unsigned long long c =
+                            deep_walk<PV>(D, bm, w0, stk, dw, X, acc, &ss, qwords, lane == 0 ? t : 0u, 1u);
+                        if (PV && lane == 0) {
+                            pv_add_at(pvc, t, d + 1, c, P.ctl, 213u);
+                            pv_add_at(pvc, d, d + 1, c, P.ctl, 214u);
+                        }
+                    }
+                } else {
+                    // root triangle (u, cand[a], cand[b]), b the r-th member of row a
+                    uint32_t lo_ = 0, hi_ = d;
+                    while (hi_ - lo_ > 1) {
+                        const uint32_t mid = (lo_ + hi_) >> 1;
+                        if (tpre[mid] <= t) lo_ = mid; else hi_ = mid;
+                    }
+                    const uint32_t a = lo_;
+                    const uint32_t* Ra = bm + (size_t)a * wp;
+                    const uint32_t b = select_above(Ra, a, t - tpre[a], wp);
+                    // the node row a & row b (k - 3 to choose) in the warp's first stack level;
+                    // lanes may still be reading the previous task's node there
+                    __syncwarp();
+                    uint32_t* C = stk;
+                    const uint32_t lo = (b + 1) >> 5;
+                    const uint32_t* Rb = bm + (size_t)b * wp;
+                    uint32_t c = 0;
+                    for (uint32_t w = lane; w < wp; w += 32) {
+                        const uint32_t x = w >= lo ? (Ra[w] & Rb[w]) : 0u;
+                        C[w] = x;
+                        c += __popc(x);
+                    }
+                    acc.words += (lane == 0) ? (wp - lo) : 0;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-                __syncwarp();
-                if (c + 3 >= k) deep_node(D, bm, C, lo, c, k - 3, stk + wp, dw, acc);
+                    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+                    __syncwarp();
+                    if (c + 3 >= k) {
+                        const WalkStart w0{C, lo, c, k - 3, false, 0u, 0u, 0u};
+                        const unsigned long long n3 = deep_walk<PV>(D, bm, w0, stk + wp, dw, X, acc, &ss, qwords,
+                                                                    lane == 0 ? a : (lane == 1 ? b : 0u), 2u);
+                        if (PV && lane == 0) {
+                            pv_add_at(pvc, a, d + 1, n3, P.ctl, 215u);
+                            pv_add_at(pvc, b, d + 1, n3, P.ctl, 216u);
+                            pv_add_at(pvc, d, d + 1, n3, P.ctl, 217u);
+                        }
+                    }
+                }
             }
+        }
+        // out of tasks: walk frames donated by the block's busy warps
+        {
+            WalkStart f;
+            uint32_t path_reg = 0, npath = 0;
+            while (deep_steal(P.ctl, &ss, qwords, wp, stk, &f, &path_reg, &npath)) {
+                const unsigned long long c =
+                    deep_walk<PV>(D, bm, f, stk + wp, dw, X, acc, &ss, qwords, path_reg, npath);
+                if (PV) {
+                    if (lane < (int)npath) pv_add_at(pvc, path_reg, d + 1, c, P.ctl, 218u);
+                    if (lane == 0) pv_add_at(pvc, d, d + 1, c, P.ctl, 219u);
+                }
             }
         }
         __syncthreads();
+        if (PV) {
+            // this block's share of the root's per-vertex counts
+            for (uint32_t i = threadIdx.x; i <= d; i += DBLOCK)
+                pv_add_at(D.pv, i < d ? cand[i] : u, D.n, pvc[i], P.ctl, 220u);
+            __syncthreads();
+        }
     }
     __syncthreads();
     if (P.n_work > P.n_big) {
-        WarpShared* ws = reinterpret_cast<WarpShared*>(smem) + warp;
-        warp_phase(P, *ws, acc);
+        if (!PV) {
+            WarpShared* ws = reinterpret_cast<WarpShared*>(smem) + warp;
+            warp_phase(P, *ws, acc);
+        } else {
+            // small roots: the root's candidate set is re-encoded directly
+            uint32_t iter = 0;
+            for (;;) {
+                uint32_t i = 0;
+                if (lane == 0) {
+                    i = P.n_big + atomicAdd(&wc->small_cursor, 1u);
+                    if ((++iter & 63u) == 0 && timed_out(P.ctl)) i = NONE;
+                }
+                i = __shfl_sync(0xffffffffu, i, 0);
+                if (i >= P.n_work) break;
+                const uint32_t u = P.roots[i];
+                const uint32_t d = small_root_rows(P, u, dw, X);
+                const unsigned long long e = warp_small<1, PV>(P.ctl, dw, X, d, k - 1, acc);
+                const unsigned long long c = warp_sum64(e);
+                for (uint32_t a = lane; a < d; a += 32) pv_add_at(D.pv, X.scand[a], D.n, X.pvm[a], P.ctl, 221u);
+                if (lane == 0) pv_add_at(D.pv, u, D.n, c, P.ctl, 222u);
+                __syncwarp();
+            }
+        }
     }
     // warp reduction (exact 128-bit), then one atomic pair per warp
     unsigned long long lo = acc.lo, hi = acc.hi, words = acc.words;
@@ -615,6 +1230,13 @@ __global__ void __launch_bounds__(DBLOCK) k_count_deep(const DeepParams D) {
     }
 }
 
+// out[v] = pv[new_of_old[v]]: per-vertex counts in the input numbering
+__global__ void k_pv_to_input(const unsigned long long* __restrict__ pv, const uint32_t* __restrict__ new_of_old,
+                              uint32_t n, unsigned long long* __restrict__ out) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        out[v] = pv[new_of_old[v]];
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -626,7 +1248,7 @@ struct DeepGeometry {
     size_t smem_bytes, gscratch_words;
 };
 
-static DeepGeometry deep_geometry(uint32_t d_max, uint32_t k, bool ec) {
+static DeepGeometry deep_geometry(uint32_t d_max, uint32_t k, bool pv) {
     DeepGeometry g;
     g.dcap = std::max<uint32_t>(d_max, 1);
     g.wp = (((g.dcap + 31) / 32) + 3) & ~3u;
@@ -635,33 +1257,39 @@ static DeepGeometry deep_geometry(uint32_t d_max, uint32_t k, bool ec) {
     uint32_t b = 6;
     while ((1u << b) < 4 * g.dcap) ++b;
     g.hash_words = g.dcap < 65535 ? (1u << b) / 2 : 0;
-    const size_t fixed = D0 + D0 + 32 + DW * (sizeof(DeepWarp) / 4) + g.hash_words;
-    const size_t region = (size_t)g.dcap * g.wp + (size_t)DW * g.wide_levels * g.wp;
+    const size_t fixed = D0 + D0 + 32 + DW * (sizeof(DeepWarp) / 4) + (size_t)DQCAP * g.wp + g.hash_words;
+    // per-vertex variant: per-warp areas and per-candidate gains stay in shared memory
+    const size_t pv_fixed = pv ? DW * (sizeof(DeepWarpPv) / 4) + 2 * (D0 + 2) : 0;
+    const size_t region = (size_t)g.dcap * g.wp * (pv ? 2 : 1) + (size_t)DW * (g.wide_levels + 1) * g.wp;
     const size_t warp_mode = sizeof(WarpShared) * NWARPS / 4;
-    if ((fixed + region) * 4 <= DEEP_SMEM_LIMIT && g.hash_words) {
+    if ((fixed + pv_fixed + region) * 4 <= DEEP_SMEM_LIMIT && g.hash_words) {
         g.in_smem = 1;
-        g.smem_bytes = std::max(fixed + region, warp_mode) * 4;
+        g.smem_bytes = std::max(fixed + pv_fixed + region, warp_mode) * 4;
         g.gscratch_words = 0;
     } else {
         g.in_smem = 0;
-        g.smem_bytes = std::max(fixed, warp_mode) * 4;
+        g.smem_bytes = std::max(fixed + pv_fixed, warp_mode) * 4;
         g.gscratch_words = (region + 63) & ~(size_t)63;
     }
-    (void)ec;
     return g;
 }
 
 typedef void (*DeepKernel)(const DeepParams);
 
-bool deep_supported(const kc_graph* g, uint32_t k) {
-    if (k < 5 || k > DEEP_MAX_K) return false;
-    const DeepGeometry geo = deep_geometry(g->d_max, k, false);
-    return geo.hash_words != 0;
+static DeepKernel deep_kernel(bool ec, bool pv) {
+    if (pv) return ec ? k_count_deep<true, true> : k_count_deep<false, true>;
+    return ec ? k_count_deep<true, false> : k_count_deep<false, false>;
 }
 
-kc_status deep_plan(const kc_graph* g, uint32_t k, bool ec, size_t* scratch_words, int* blocks_out) {
-    const DeepGeometry geo = deep_geometry(g->d_max, k, ec);
-    DeepKernel kern = ec ? k_count_deep<true> : k_count_deep<false>;
+bool deep_supported(const kc_graph* g, uint32_t k, bool pv) {
+    if (k > DEEP_MAX_K || k < (pv ? 3u : 5u)) return false;
+    const DeepGeometry geo = deep_geometry(g->d_max, k, pv);
+    return geo.hash_words != 0 && geo.smem_bytes <= DEEP_SMEM_LIMIT;
+}
+
+kc_status deep_plan(const kc_graph* g, uint32_t k, bool ec, bool pv, size_t* scratch_words, int* blocks_out) {
+    const DeepGeometry geo = deep_geometry(g->d_max, k, pv);
+    DeepKernel kern = deep_kernel(ec, pv);
     KC_CUDA(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.smem_bytes));
     int bps = 0;
     KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, DBLOCK, geo.smem_bytes));
@@ -672,12 +1300,14 @@ kc_status deep_plan(const kc_graph* g, uint32_t k, bool ec, size_t* scratch_word
 }
 
 kc_status deep_launch(kc_graph* g, uint32_t k, bool ec, uint32_t n_big, uint32_t n_work, uint32_t* task_next,
-                      uint32_t* task_total, uint32_t* gscratch, Ctl* ctl, cudaStream_t s) {
-    const DeepGeometry geo = deep_geometry(g->d_max, k, ec);
-    DeepKernel kern = ec ? k_count_deep<true> : k_count_deep<false>;
+                      uint32_t* task_total, uint32_t* gscratch, unsigned long long* pv, Ctl* ctl, cudaStream_t s) {
+    const bool pvon = pv != nullptr;
+    if (pvon && k < 4) ec = false;  // an edge-centric task at k = 3 is a single clique
+    const DeepGeometry geo = deep_geometry(g->d_max, k, pvon);
+    DeepKernel kern = deep_kernel(ec, pvon);
     int blocks = 0;
     size_t sw = 0;
-    KC_CHECK(deep_plan(g, k, ec, &sw, &blocks));
+    KC_CHECK(deep_plan(g, k, ec, pvon, &sw, &blocks));
     DeepParams D;
     memset(&D, 0, sizeof(D));
     CountParams& P = D.base;
@@ -700,7 +1330,18 @@ kc_status deep_launch(kc_graph* g, uint32_t k, bool ec, uint32_t n_big, uint32_t
     D.wp = geo.wp;
     D.wide_levels = geo.wide_levels;
     D.task_total = task_total;
+    D.pv = pv;
+    D.n = g->n;
     kern<<<blocks, DBLOCK, geo.smem_bytes, s>>>(D);
+    note_launch();
+    KC_CUDA(cudaGetLastError());
+    return KC_OK;
+}
+
+kc_status pv_to_input(const kc_graph* g, const unsigned long long* pv, uint64_t* out, cudaStream_t s) {
+    if (g->n == 0) return KC_OK;
+    k_pv_to_input<<<std::max(1, g->sm_count * 4), 256, 0, s>>>(pv, (const uint32_t*)g->new_of_old.ptr, g->n,
+                                                               (unsigned long long*)out);
     note_launch();
     KC_CUDA(cudaGetLastError());
     return KC_OK;

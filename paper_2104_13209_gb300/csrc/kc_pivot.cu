@@ -50,6 +50,7 @@ struct PivotParams {
     const uint32_t* roots;       // library ids, decreasing out-degree
     uint32_t n_big;              // roots[0, n_big): |C| > 32
     uint32_t n_work;             // roots[n_big, n_work): 32 >= |C| >= dmin
+    uint32_t n;                  // vertices (per-vertex accumulators)
     uint32_t* task_next;         // per big root: next unclaimed branch (zeroed)
     uint32_t kfix;               // 0 = every size; else only size kfix is needed
     uint32_t pvk;                // per-vertex size (0 = none)
@@ -109,6 +110,7 @@ __device__ __forceinline__ void pv_gain(const PivotParams& P, uint32_t vid, unsi
         atomicOr(&P.ctl->flags, (unsigned)KC_FLAG_VERTEX_OVERFLOW);
         return;
     }
+    if (!in_bounds(P.ctl, vid, P.n, 101u)) return;
     unsigned long long old = atomicAdd(&P.pv[vid], g);
     if (old + g < old) atomicOr(&P.ctl->flags, (unsigned)KC_FLAG_VERTEX_OVERFLOW);
 }
@@ -233,7 +235,10 @@ __device__ __forceinline__ void leaf(const PivotParams& P, LeafCache& lc, uint32
         if (c && gP) {
             for (uint32_t w = 0; w < W; ++w) {
                 uint32_t bits = S[w];
-                if (lane < __popc(bits)) pv_gain(P, cand[(w << 5) + __fns(bits, 0, lane + 1)], gP);
+                if (lane < __popc(bits)) {
+                    const uint32_t pos = (w << 5) + __fns(bits, 0, lane + 1);
+                    if (in_bounds(P.ctl, pos, W == 1 ? 32u : P.dcap, 102u)) pv_gain(P, cand[pos], gP);
+                }
             }
         }
         sumH = sat_add(sumH, gH);
@@ -1289,6 +1294,7 @@ static kc_status pivot_run(kc_graph* g, uint32_t kfix, uint32_t cap, uint32_t pv
     P.roots = (const uint32_t*)g->roots.ptr;
     P.n_big = (uint32_t)n_big;
     P.n_work = (uint32_t)n_work;
+    P.n = n;
     P.task_next = tasks;
     P.kfix = kfix;
     P.pvk = pvon ? pvk : 0;

@@ -132,3 +132,22 @@ def test_time_limit_returns_timeout_and_keeps_the_handle():
     G.set_time_limit(0)
     drp, dci, _, _ = O.dag_for(g.row_ptr, g.col_idx, "degeneracy")
     assert G.count(3).total == O.count_orient(drp, dci, 3).total
+
+
+@pytest.mark.parametrize("gi", range(3))
+def test_per_vertex_orientation_mode(gi):
+    """Per-vertex counts from the orientation traversal (pivot = 0): every
+    vertex's number of k-cliques, against the oracle's per-vertex counts."""
+    # sizes chosen so that the oracle's per-vertex route (one step per clique)
+    # stays within seconds
+    g, ks = [(synth.rmat(12, 16, seed=1), (3, 4, 5, 6, 7)), (synth.dense_random_graph(120, 0.6, 2), (3, 4, 5, 6, 7, 8)),
+             (synth.chung_lu_planted(20000, 2.1, 10, 20, 20, 60, 0.9, seed=1), (3, 4, 5, 6))][gi]
+    drp, dci, _, _ = O.dag_for(g.row_ptr, g.col_idx, "degeneracy")
+    G = graph(g)
+    for k in ks:
+        want = O.count_orient(drp, dci, k, per_vertex=True)
+        for scheme in ("vc", "ec"):
+            tot, pv, fl = G.count_per_vertex(k, pivot=False, scheme=scheme)
+            assert tot == want.total, (k, scheme)
+            assert [int(x) for x in pv] == want.per_vertex, (k, scheme)
+            assert int(pv.sum()) == k * want.total

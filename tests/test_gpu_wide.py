@@ -98,14 +98,16 @@ def test_multipartite_wide_orientation(k):
 
 @pytest.mark.parametrize("k", [3, 5, 8])
 def test_multipartite_wide_per_vertex(k):
+    # both traversals: pivoting, and orientation mode with either split
     G = graph(multipartite())
-    tot, pv, fl = G.count_per_vertex(k)
-    assert tot == elementary_symmetric(PARTS, k)
     label = np.repeat(np.arange(len(PARTS)), PARTS)
-    for part in range(len(PARTS)):
-        others = PARTS[:part] + PARTS[part + 1:]
-        want = elementary_symmetric(others, k - 1)
-        assert np.all(pv[label == part] == want), (k, part)
+    for pivot, scheme in ((True, "auto"), (False, "vc"), (False, "ec")):
+        tot, pv, fl = G.count_per_vertex(k, pivot=pivot, scheme=scheme)
+        assert tot == elementary_symmetric(PARTS, k)
+        for part in range(len(PARTS)):
+            others = PARTS[:part] + PARTS[part + 1:]
+            want = elementary_symmetric(others, k - 1)
+            assert np.all(pv[label == part] == want), (k, part, pivot, scheme)
 
 
 @pytest.mark.parametrize("orient", ["degeneracy", "degree"])
@@ -120,6 +122,24 @@ def test_global_scratch_orientation_deep(orient):
             for sw in ((1, 8, 32) if k <= 4 else (0,)):
                 got = G.count(k, scheme=scheme, subwarp=sw).total
                 assert got == want, (orient, k, scheme, sw)
+
+
+def test_global_scratch_per_vertex_orientation():
+    # per-vertex counts with 1,400-wide candidate sets (bitmaps, transposes
+    # and stacks in global memory).  The join identity per vertex: a vertex v
+    # of C is in c_k^C(v) + 1500 c_{k-1}^C(v) k-cliques, an independent vertex
+    # in c_{k-1}(C); c^C(v) from the oracle's per-vertex counts on C.
+    c = sparse_core()
+    cdrp, cdci, _, _ = O.dag_for(c.row_ptr, c.col_idx, "degeneracy")
+    G = graph(join_indep())
+    for k in (3, 4, 5, 6):
+        pk = O.count_orient(cdrp, cdci, k, per_vertex=True).per_vertex
+        pk1 = O.count_orient(cdrp, cdci, k - 1, per_vertex=True).per_vertex
+        want = [a + B_INDEP * b for a, b in zip(pk, pk1)] + [core_counts(12)[k - 1]] * B_INDEP
+        for scheme in ("vc", "ec"):
+            tot, pv, fl = G.count_per_vertex(k, pivot=False, scheme=scheme)
+            assert tot == join_count(k), (k, scheme)
+            assert [int(x) for x in pv] == want, (k, scheme)
 
 
 def test_global_scratch_pivot():

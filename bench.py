@@ -33,8 +33,7 @@ CACHE = os.path.join(ROOT, "paper_2104_13209_gb300", "_build", "cache")
 PROFILES = os.path.join(ROOT, "profiles")
 L2_FLUSH_BYTES = 512 << 20   # larger than the 129 MB L2
 POPC_PER_SM_CLK = 16         # population count results per SM per clock (CUDA arithmetic throughput table)
-SMS = 152
-SM_MAX_HZ = 2.07e9
+ISSUE_PER_SM_CLK = 4         # warp instructions issued per SM per clock (four schedulers)
 METRIC = "k-clique count time & cliques/s (k=4/7/10); batched/served queries/s, p99 vs plain"
 
 
@@ -211,7 +210,7 @@ def run_reference(a, g, plan, world, rank):
 # our arm
 # ----------------------------------------------------------------------------
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2104_13209_gb300", "csrc", f)
-                  for f in ("kc_count.cu", "kc_bitmap.cuh", "kc_common.cuh")]
+                  for f in ("kc_count.cu", "kc_dfs.cuh", "kc_bitmap.cuh", "kc_common.cuh")]
 
 
 def kernel_source_hash() -> str:
@@ -221,17 +220,18 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_record():
-    """DRAM bytes per launch of the count kernel from profiles/traffic.json,
-    if the kernel's sources are unchanged since the counters were taken."""
+def traffic_record() -> dict:
+    """Counters of the count kernel from profiles/traffic.json (DRAM bytes
+    and warp instructions per launch), if the kernel's sources are unchanged
+    since they were taken; else {}."""
     path = os.path.join(PROFILES, "traffic.json")
     if not os.path.exists(path):
-        return None
+        return {}
     with open(path) as f:
         rec = json.load(f)
     if rec.get("kernel_source_sha256_16") != kernel_source_hash():
-        return None
-    return rec.get("dram_bytes_per_launch")
+        return {}
+    return rec
 
 
 def algorithmic_bytes(drp, dci, k: int) -> float:
@@ -244,9 +244,64 @@ def algorithmic_bytes(drp, dci, k: int) -> float:
     return float(4 * (d[roots].sum() + d[dci.astype(np.int64)][roots[src]].sum()))
 
 
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        return json.load(f)
+
+
 def measured_hbm_gbs() -> float:
-    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-        return float(json.load(f)["hbm_gbs"])
+    return float(measured_peaks()["hbm_gbs"])
+
+
+def device_rates(dev_index: int) -> dict:
+    """SM count (device attribute) and the maximum SM clock (the measured
+    peaks record, else nvidia-smi), and the integer-pipe and issue peaks
+    derived from them."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
+    mhz = measured_peaks().get("sm_max_mhz")
+    src = "MEASURED_PEAKS.json sm_max_mhz"
+    if not mhz:
+        try:
+            out = subprocess.run(["nvidia-smi", "-i", str(dev_index), "--query-gpu=clocks.max.sm",
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+            mhz = float(out.stdout.strip().splitlines()[0])
+            src = "nvidia-smi clocks.max.sm"
+        except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+            mhz, src = 2070.0, "nominal maximum"
+    hz = float(mhz) * 1e6
+    return {"sms": sms, "sm_hz": hz, "clock_source": src,
+            "alu_tops": 2.0 * sms * POPC_PER_SM_CLK * hz / 1e12,
+            "issue_ginst": sms * ISSUE_PER_SM_CLK * hz / 1e9,
+            "alu_note": f"derived: {sms} SMs x {POPC_PER_SM_CLK} popc/clk x {hz / 1e9:.2f} GHz x 2 ops "
+                        "(AND + POPC) per word",
+            "issue_note": f"derived: {sms} SMs x {ISSUE_PER_SM_CLK} warp instructions/clk x {hz / 1e9:.2f} GHz"}
+
+
+def measured_l2_read_gbs(dev) -> float:
+    """Read bandwidth of the L2: a 48 MiB buffer (resident in the 129 MB L2)
+    summed 20 times per timing, best of 8 (a lower bound of the peak)."""
+    import torch
+
+    x = torch.ones(12 << 20, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        x.sum()
+    torch.cuda.synchronize()
+    best = 0.0
+    for _ in range(8):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            x.sum()
+        e1.record()
+        e1.synchronize()
+        best = max(best, 20 * x.numel() * 4 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    return best
 
 
 def run_ours(a, g, plan, world, rank, local_rank):
@@ -347,33 +402,77 @@ def run_ours(a, g, plan, world, rank, local_rank):
 
     # roofline of the dominant kernel (the first count of the plan): the
     # slower of its algorithmic CSR bytes at HBM bandwidth and its AND + POPC
-    # word operations at the population-count pipe's peak
+    # word operations at the population-count pipe's peak (the model's two
+    # terms), with the terms that show its actual limiter beside them: the
+    # same bytes at the measured L2 read bandwidth (the DAG stays resident in
+    # L2) and its issued warp instructions at the issue peak (ncu counters)
     k0, s0 = plan[0]
     lab0 = f"k{k0}{s0}"
     t_cnt = per_label[lab0] / 1e3
     with torch.cuda.stream(stream):
         G = kclique.Graph(rp_d, ci_d, n=n, orient="degeneracy", validate=False, stream=stream)
         drp, dci, _, _ = G.export()
-        G.close()
     b_alg = algorithmic_bytes(drp, dci, k0)
     ops = 2.0 * res[0].words            # one AND + one POPC per 32-bit bitmap word
+    rates = device_rates(local_rank)
     peak_hbm = measured_hbm_gbs()
-    peak_alu = 2.0 * SMS * POPC_PER_SM_CLK * SM_MAX_HZ / 1e12
+    peak_alu = rates["alu_tops"]
+    peak_l2 = measured_l2_read_gbs(dev)
     t_hbm = b_alg / (peak_hbm * 1e9)
     t_alu = ops / (peak_alu * 1e12)
-    traffic = traffic_record()
+    rec = traffic_record()
     terms = {"hbm": {"bytes": b_alg, "achieved_gbs": b_alg / t_cnt / 1e9, "peak_gbs": peak_hbm,
                      "roof_ms": 1e3 * t_hbm},
              "alu": {"ops": ops, "achieved_tops": ops / t_cnt / 1e12, "peak_tops": peak_alu, "roof_ms": 1e3 * t_alu,
-                     "peak_note": "derived: 152 SMs x 16 popc/clk x 2.07 GHz x 2 ops (AND + POPC) per word"}}
+                     "peak_note": rates["alu_note"]},
+             "l2": {"bytes": b_alg, "achieved_gbs": b_alg / t_cnt / 1e9, "peak_gbs": peak_l2,
+                    "roof_ms": 1e3 * b_alg / (peak_l2 * 1e9),
+                    "peak_note": "measured here: a 48 MiB L2-resident buffer read by a reduction (lower bound)"}}
+    if rec.get("warp_inst_per_launch"):
+        inst = float(rec["warp_inst_per_launch"])
+        terms["issue"] = {"warp_inst": inst, "achieved_ginst_s": inst / t_cnt / 1e9,
+                          "peak_ginst_s": rates["issue_ginst"], "roof_ms": 1e3 * inst / (rates["issue_ginst"] * 1e9),
+                          "peak_note": rates["issue_note"], "source": "profiles/traffic.json (ncu)"}
     if t_hbm >= t_alu:
         roof = {"bound": "hbm", "achieved": terms["hbm"]["achieved_gbs"], "peak": peak_hbm, "unit": "GB/s"}
     else:
         roof = {"bound": "alu", "achieved": terms["alu"]["achieved_tops"], "peak": peak_alu, "unit": "Tops/s"}
-    roof.update({"frac": roof["achieved"] / roof["peak"], "traffic": traffic,
+    limiter = max(terms, key=lambda x: terms[x]["roof_ms"] / (1e3 * t_cnt) if x != "hbm" else 0.0)
+    roof.update({"frac": roof["achieved"] / roof["peak"], "traffic": rec.get("dram_bytes_per_launch"),
                  "kernel": f"k_count_orient ({lab0})", "kernel_ms": 1e3 * t_cnt, "terms": terms,
+                 "closest_term": limiter,
                  "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if roof["bound"] == "hbm"
                  else "derived from unit counts and clock"})
+
+    # the deep sizes of the same configuration: one count of size k_deep
+    # (edge-centric, the choice for k >= 6), after a k = 5 count that loads
+    # the same kernel
+    deep = None
+    if a.deep_k:
+        kd = a.deep_k
+        rr = torch.zeros(kclique.RESULT_BYTES, dtype=torch.uint8, device=dev)
+        with torch.cuda.stream(stream):
+            G.count_async(5, rr, scheme="ec", stream=stream)
+        stream.synchronize()
+        launches_d0 = kclique.launch_count()
+        with ClockSampler(local_rank) as clk_d:
+            with torch.cuda.stream(stream):
+                d0 = torch.cuda.Event(enable_timing=True)
+                d1 = torch.cuda.Event(enable_timing=True)
+                d0.record(stream)
+                G.count_async(kd, rr, scheme="ec", stream=stream)
+                d1.record(stream)
+            stream.synchronize()
+        rd = kclique.parse_result(bytes(rr.cpu().numpy()))
+        dms = d0.elapsed_time(d1)
+        dops = 2.0 * rd.words
+        deep = {"k": kd, "scheme": "ec", "status": kclique.status_name(rd.status), "count": str(rd.total),
+                "ms": dms, "cliques_per_s": rd.total / (dms / 1e3), "gpu_launches": kclique.launch_count() - launches_d0,
+                "roofline": {"bound": "alu", "achieved": dops / (dms / 1e3) / 1e12, "peak": peak_alu,
+                             "unit": "Tops/s", "frac": dops / (dms / 1e3) / 1e12 / peak_alu,
+                             "kernel": "k_count_deep<EC> (one launch)", "ops": dops, "peak_note": rates["alu_note"]},
+                "clocks": clk_d.summary()}
+    G.close()
 
     clocks = clk.summary()
     value = replica_throughput(total_cliques, step_ms / 1e3, world)
@@ -404,13 +503,14 @@ def run_ours(a, g, plan, world, rank, local_rank):
         "clocks": clocks,
         "gpu_launches": launches,
     }
+    if deep is not None:
+        line[f"k{deep['k']}"] = deep
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cb = oracle_sample_rate(g, k0, a.cpu_budget)
         line["cpu_baseline"] = {"value": cb["rate"], "unit": "cliques/s", "cores": cb["threads"], "kind": "oracle",
                                 "sample": f"k={k0}: every {cb['stride']}-th root with out-degree >= {k0 - 1} "
                                           f"({cb['roots']} roots, {cb['seconds']:.1f} s)"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 # ----------------------------------------------------------------------------
@@ -486,7 +586,8 @@ def run_batch(a, world, rank, local_rank):
         r2 = B.count(gid, ks, tune=tune, stream=stream)
         e2e.append(time.perf_counter() - t0)
     assert [r.total for r in r2] == [r.total for r in got]
-    peak = 2.0 * SMS * POPC_PER_SM_CLK * SM_MAX_HZ / 1e12
+    rates = device_rates(local_rank)
+    peak = rates["alu_tops"]
     achieved = 2.0 * words / (step_ms / 1e3) / 1e12
     line = {
         "metric": METRIC, "value": nq / (step_ms / 1e3), "unit": "queries/s", "n_gpus": world, "steps": a.steps,
@@ -501,8 +602,7 @@ def run_batch(a, world, rank, local_rank):
         "e2e": {"value": nq / float(np.mean(e2e)), "unit": "queries/s", "h2d_bytes_per_step": nq * 56,
                 "d2h_bytes_per_step": nq * kclique.RESULT_BYTES},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_count_batch (whole step)",
-                     "peak_note": "derived: 152 SMs x 16 popc/clk x 2.07 GHz x 2 ops (AND + POPC) per word"},
+                     "traffic": None, "kernel": "k_count_batch (whole step)", "peak_note": rates["alu_note"]},
         "clocks": clk.summary(), "gpu_launches": launches,
     }
     if not a.no_cpu_baseline:
@@ -517,7 +617,7 @@ def run_batch(a, world, rank, local_rank):
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": done / dt, "unit": "queries/s", "cores": O.default_threads(),
                                 "kind": "oracle", "sample": f"the first {done} queries ({dt:.1f} s)"}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_serve(a, world, rank, local_rank):
@@ -536,7 +636,10 @@ def run_serve(a, world, rank, local_rank):
     ts, gq, kq, pq = workloads.query_stream(a.rate, a.serve_seconds, len(gs))
     out = {}
     for mode in a.serve_modes.split(","):
-        S = kclique.Server(hbm_budget=200 << 30, max_batch=256, slots=4, serial=(mode == "plain"))
+        # both modes choose the traversal by k (Section 4.5); the continuous-
+        # batching server also refuses shapes that ran out of time before
+        S = kclique.Server(hbm_budget=200 << 30, max_batch=256, slots=4, serial=(mode == "plain"),
+                           auto_traversal=True, refuse_expensive=(mode != "plain"))
         S.set_time_limit(a.time_limit)
         for h in gs:
             S.add_graph(h)
@@ -551,12 +654,16 @@ def run_serve(a, world, rank, local_rank):
             tickets.append(S.submit(int(gq[i]), int(kq[i]), bool(pq[i])))
         rs = [S.poll(t, -1) for t in tickets]
         wall = time.perf_counter() - t0
-        lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in rs])
+        ok = [r for r in rs if r["status"] == kclique.KC_OK]
+        lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in ok]) if ok else np.zeros(1)
         span = (max(r["t_done_ms"] for r in rs) - min(r["t_submit_ms"] for r in rs)) / 1e3
-        out[mode] = {"queries": len(rs), "qps": len(rs) / span, "p50_ms": float(np.percentile(lat, 50)),
-                     "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+        out[mode] = {"queries": len(rs), "completed": len(ok), "qps": len(ok) / span,
+                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "mean_ms": float(lat.mean()), "latency_over": "completed queries",
                      "timeouts": int(sum(r["status"] == kclique.KC_E_TIMEOUT for r in rs)),
-                     "errors": int(sum(r["status"] not in (kclique.KC_OK, kclique.KC_E_TIMEOUT) for r in rs)),
+                     "refused": int(sum(r["status"] == kclique.KC_E_REFUSED for r in rs)),
+                     "errors": int(sum(r["status"] not in (kclique.KC_OK, kclique.KC_E_TIMEOUT, kclique.KC_E_REFUSED)
+                                       for r in rs)),
                      "launches": S.stats()["launches"] - min(64, len(ts)), "wall_s": wall,
                      "totals": [r["total"] if r["status"] == kclique.KC_OK else None for r in rs]}
         S.close()
@@ -572,13 +679,14 @@ def run_serve(a, world, rank, local_rank):
         "warmup": 1, "ms_per_step": 1e3 * out[main_mode]["wall_s"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": f"serving: pool of {len(gs)} graphs (16 ER, 24 R-MAT 14-18, 24 Chung-Lu 100k-1M), "
-                               f"Poisson {a.rate:g} req/s for {a.serve_seconds:g} s, k uniform 3..12, pivot p=0.5",
+                               f"Poisson {a.rate:g} req/s for {a.serve_seconds:g} s, k uniform 3..12, pivot p=0.5 "
+                               "(the server picks the traversal by k)",
                    "time_limit_s": a.time_limit, "max_batch": 256, "slots": 4},
         "latency_ms": {"p50": out[main_mode]["p50_ms"], "p99": out[main_mode]["p99_ms"]},
         "served": {m: {k: v for k, v in out[m].items() if k != "totals"} for m in modes},
         "mismatches": mismatch,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -596,6 +704,10 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--time-limit", type=float, default=0.25)
     ap.add_argument("--serve-modes", default="batched,plain")
+    ap.add_argument("--sub", default="batch,serve",
+                    help="sub-records of the default line: batch, serve (one GPU only; empty: none)")
+    ap.add_argument("--deep-k", type=int, default=7,
+                    help="also time one count of this size on the same graph (0: skip)")
     a = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -607,17 +719,29 @@ def main():
         backend = "nccl" if torch.cuda.is_available() else "gloo"
         dist.init_process_group(backend=backend)
     if a.workload == "batch" and a.impl == "ours":
-        run_batch(a, world, rank, local_rank)
+        print(json.dumps(run_batch(a, world, rank, local_rank)), flush=True)
         return
     if a.workload == "serve" and a.impl == "ours":
-        run_serve(a, world, rank, local_rank)
+        print(json.dumps(run_serve(a, world, rank, local_rank)), flush=True)
         return
     g = workload_graph(a.scale)
     plan = parse_plan(a.plan)
     if a.impl == "reference":
         run_reference(a, g, plan, world, rank)
     else:
-        run_ours(a, g, plan, world, rank, local_rank)
+        line = run_ours(a, g, plan, world, rank, local_rank)
+        # the batched and serving workloads of the same metric, as sub-records
+        # of the one line (one GPU only: they are not replicated)
+        subs = [x for x in a.sub.split(",") if x] if world == 1 else []
+        if "batch" in subs:
+            b = run_batch(a, world, rank, local_rank)
+            line["batched"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "config", "plain", "e2e",
+                                                 "roofline", "clocks", "gpu_launches", "cpu_baseline") if k in b}
+        if "serve" in subs:
+            sv = run_serve(a, world, rank, local_rank)
+            line["served"] = {k: sv[k] for k in ("value", "unit", "config", "latency_ms", "served", "mismatches")}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
 

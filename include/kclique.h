@@ -50,6 +50,7 @@ typedef int kc_status;
 #define KC_E_CUDA 6            /* a CUDA runtime call failed */
 #define KC_E_INTERNAL 7        /* a device-side consistency check failed */
 #define KC_E_UNSUPPORTED 8     /* a size or case beyond what the library handles */
+#define KC_E_REFUSED 9         /* a serving query not admitted: its shape ran out of time before */
 
 /* ---- enumerations ------------------------------------------------------ */
 /* Orientation criterion (Section 3.1). */
@@ -341,11 +342,21 @@ typedef struct kc_server_result {
 
 /* One launch in flight at a time, one query per launch (the plain baseline). */
 #define KC_SERVER_SERIAL 1
+/* The server picks the traversal of every query by the paper's guideline
+ * (Section 4.5): graph orientation below k = 7, pivoting from k = 7.  The
+ * query's own pivot flag is then only recorded (the count is the same). */
+#define KC_SERVER_AUTO_TRAVERSAL 2
+/* Admission control: a query is refused at once (KC_E_REFUSED) when an
+ * earlier query of the same graph, k and traversal ran out of the time
+ * limit, instead of waiting for a slot and timing out again. */
+#define KC_SERVER_REFUSE_EXPENSIVE 4
 
 /* hbm_budget: device bytes the server may keep resident (slots and graphs);
  * a graph that would exceed it is refused with KC_E_NO_MEMORY.
  * max_batch >= 1 queries per batched launch; slots >= 1 launches in flight.
- * flags: 0 or KC_SERVER_SERIAL.  The calling thread's current
+ * flags: 0 or a combination of KC_SERVER_SERIAL (one launch at a time, in
+ *   arrival order: the plain baseline), KC_SERVER_AUTO_TRAVERSAL and
+ *   KC_SERVER_REFUSE_EXPENSIVE.  The calling thread's current
  * device is the server's. */
 kc_status kc_server_create(size_t hbm_budget, uint32_t max_batch, uint32_t slots, int flags, kc_server** out);
 

@@ -97,6 +97,7 @@ const char* kc_status_name(kc_status s) {
         case KC_E_CUDA: return "KC_E_CUDA";
         case KC_E_INTERNAL: return "KC_E_INTERNAL";
         case KC_E_UNSUPPORTED: return "KC_E_UNSUPPORTED";
+        case KC_E_REFUSED: return "KC_E_REFUSED";
         default: return "KC_E_UNKNOWN";
     }
 }

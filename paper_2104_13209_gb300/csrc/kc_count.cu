@@ -327,7 +327,7 @@ __device__ void block_root(const CountParams& P, const uint32_t* __restrict__ rp
     uint32_t* stk_base = qwords + (size_t)QCAP * W0;
     uint32_t* own = stk_base + (size_t)(threadIdx.x / G) * (P.depth + 1) * W0;  // a taken frame's list
     uint32_t* stk = own + W0;                                                    // child lists
-    uint16_t* tab = reinterpret_cast<uint16_t*>(stk_base + (size_t)(BLOCK / G) * (P.depth + 1) * W0);
+    uint32_t* tab = stk_base + (size_t)(BLOCK / G) * (P.depth + 1) * W0;
     const unsigned gm = group_mask<G>();
     const unsigned gl = threadIdx.x & (G - 1);
     const unsigned leader = (threadIdx.x & 31) & ~(unsigned)(G - 1);
@@ -556,11 +556,7 @@ struct Geometry {
 };
 
 // 16-bit slots of the candidate position table for candidate sets up to dcap
-static uint32_t hash_words_for(uint32_t dcap) {
-    uint32_t b = 6;
-    while ((1u << b) < 4 * dcap) ++b;
-    return (1u << b) / 2;
-}
+static uint32_t hash_words_for(uint32_t dcap) { return hash_table_words(dcap); }
 
 static Geometry plan_geometry(uint32_t dcap, uint32_t k, uint32_t G, bool ec) {
     Geometry g;

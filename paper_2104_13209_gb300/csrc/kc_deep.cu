@@ -150,26 +150,67 @@ __device__ __forceinline__ uint32_t mask_pop(Mask<NW>& a) {
     return NONE;
 }
 
-// Edges of the sub-graph induced by J (rows T, nw words each).  PV: each
-// member gains its degree in that sub-graph (out-neighbours from T, in-
-// neighbours from the transpose TT).
+// popc(J & row) over words i..NW-1 (row: a re-encoded row whose member
+// lies in word i, so its words below i are zero)
+template <int NW, int I>
+__device__ __forceinline__ uint32_t popc_from(const Mask<NW>& J, const uint32_t* row) {
+    uint32_t c = 0;
+    if (NW == 4 && I <= 1) {
+        const uint4 x = *reinterpret_cast<const uint4*>(row);
+        if (I == 0) c += __popc(J.w[0] & x.x);
+        c += __popc(J.w[1 % NW] & x.y) + __popc(J.w[2 % NW] & x.z) + __popc(J.w[3 % NW] & x.w);
+    } else if (NW == 4 && I == 2) {
+        const uint2 x = *reinterpret_cast<const uint2*>(row + 2);
+        c += __popc(J.w[2 % NW] & x.x) + __popc(J.w[3 % NW] & x.y);
+    } else if (NW == 2 && I == 0) {
+        const uint2 x = *reinterpret_cast<const uint2*>(row);
+        c += __popc(J.w[0] & x.x) + __popc(J.w[1 % NW] & x.y);
+    } else {
+        c += __popc(J.w[I % NW] & row[I % NW]);  // the last word
+    }
+    return c;
+}
+
+// sum over the members v of J in word I of popc(J & T[v]) (one lane)
+template <int NW, int I>
+__device__ __forceinline__ uint32_t edges_in_word(const Mask<NW>& J, const uint32_t* T) {
+    uint32_t s = 0, bits = J.w[I % NW];
+    while (bits) {
+        const uint32_t v = I * 32 + (__ffs(bits) - 1);
+        bits &= bits - 1;
+        s += popc_from<NW, I>(J, T + (size_t)v * NW);
+    }
+    return s;
+}
+
+// Edges of the sub-graph induced by J (rows T, nw words each): members in
+// word i only need the row words from i on (rows are upper triangular).
+// PV: each member gains its degree in that sub-graph (out-neighbours from
+// T, in-neighbours from the transpose TT).
 template <int NW, bool PV>
 __device__ __forceinline__ unsigned long long lane_edges(Mask<NW> J, const uint32_t* T, const PvCtx& X, const Ctl* ctl,
                                                          unsigned long long& words) {
-    const Mask<NW> J0 = J;
-    unsigned long long s = 0;
-    for (;;) {
-        const uint32_t v = mask_pop<NW>(J);
-        if (v == NONE) break;
-        const uint32_t out = mask_popc<NW>(mask_and<NW>(J, T + (size_t)v * NW));
-        s += out;
-        words += NW;
-        if (PV) {
+    if (PV) {
+        const Mask<NW> J0 = J;
+        unsigned long long s = 0;
+        for (;;) {
+            const uint32_t v = mask_pop<NW>(J);
+            if (v == NONE) break;
+            const uint32_t out = mask_popc<NW>(mask_and<NW>(J, T + (size_t)v * NW));
+            s += out;
             const uint32_t in = mask_popc<NW>(mask_and<NW>(J0, X.TT + (size_t)v * NW));
             pv_add_at(X.pvm, v, CMAX, out + in, ctl, 201u);
-            words += NW;
+            words += 2 * NW;
         }
+        return s;
     }
+    uint32_t s = edges_in_word<NW, 0>(J, T);
+    if (NW > 1) s += edges_in_word<NW, 1>(J, T);
+    if (NW > 2) {
+        s += edges_in_word<NW, 2>(J, T);
+        s += edges_in_word<NW, 3>(J, T);
+    }
+    words += (unsigned long long)mask_popc<NW>(J) * NW;
     return s;
 }
 
@@ -1027,8 +1068,8 @@ __global__ void __launch_bounds__(DBLOCK) k_count_deep(const DeepParams D) {
     uint32_t* tpre = cand + D0;                                      // D0 + 32 words
     DeepWarp* dws = reinterpret_cast<DeepWarp*>(tpre + D0 + 32);
     uint32_t* qwords = reinterpret_cast<uint32_t*>(dws + DW);        // DQCAP x wp words
-    uint16_t* tab = reinterpret_cast<uint16_t*>(qwords + (size_t)DQCAP * wp);
-    uint32_t* after_tab = reinterpret_cast<uint32_t*>(tab) + P.hash_words;
+    uint32_t* tab = qwords + (size_t)DQCAP * wp;
+    uint32_t* after_tab = tab + P.hash_words;
     uint32_t* region = P.in_smem ? after_tab : P.gscratch + (size_t)blockIdx.x * P.gscratch_words;
     uint32_t* bm = region;
     uint32_t* wide = bm + (size_t)P.dcap * wp;
@@ -1254,9 +1295,7 @@ static DeepGeometry deep_geometry(uint32_t d_max, uint32_t k, bool pv) {
     g.wp = (((g.dcap + 31) / 32) + 3) & ~3u;
     g.wide_levels = k;  // wide levels above the re-encoded ones: fewer than k
     const size_t D0 = (g.dcap + 31) & ~31u;
-    uint32_t b = 6;
-    while ((1u << b) < 4 * g.dcap) ++b;
-    g.hash_words = g.dcap < 65535 ? (1u << b) / 2 : 0;
+    g.hash_words = g.dcap < 65535 ? hash_table_words(g.dcap) : 0;
     const size_t fixed = D0 + D0 + 32 + DW * (sizeof(DeepWarp) / 4) + (size_t)DQCAP * g.wp + g.hash_words;
     // per-vertex variant: per-warp areas and per-candidate gains stay in shared memory
     const size_t pv_fixed = pv ? DW * (sizeof(DeepWarpPv) / 4) + 2 * (D0 + 2) : 0;

@@ -199,6 +199,144 @@ __device__ __forceinline__ void peel_take(bool pred, uint32_t v, uint32_t round,
     }
 }
 
+// Loop state of the peel, the same in every thread of the cluster.
+struct PeelState {
+    uint32_t level, round, p, max_level;
+    uint32_t nf;    // items of the frontier the next process phase reads
+    uint32_t rn;    // entries of the remaining list the next scan reads
+    uint32_t fail;  // KC_FLAG_* when the loop stopped on an inconsistency
+    int fb;         // frontier buffer the next phase pushes into
+    int pf;         // frontier buffer the next process phase reads
+    int rl;         // remaining list the next scan reads
+    int all;        // the next scan reads every vertex (the first one)
+    int scan;       // kind of the next phase
+    int done;
+};
+
+// Phases at most this large run in the cluster's first block alone, with
+// block barriers between them, while the other blocks wait at one cluster
+// barrier: most of the peel's phases are tiny frontiers of the long tail.
+static constexpr uint32_t SOLO_SCAN = 8192;   // remaining-list entries of a scan
+static constexpr uint32_t SOLO_ITEMS = 1024;  // frontier items of a process phase
+
+__device__ __forceinline__ bool peel_small(const PeelState& S) {
+    return S.scan ? S.rn <= SOLO_SCAN : S.nf <= SOLO_ITEMS;
+}
+
+// One phase of the peel by the threads given (gwarp of nwarps warps):
+// adds to the control slot wr.
+__device__ __forceinline__ void peel_phase(const PeelState& S, uint32_t gwarp, uint32_t nwarps,
+                                           const uint32_t* __restrict__ rp, const uint32_t* __restrict__ ci,
+                                           uint32_t n, int* deg, uint32_t* round_of, uint32_t* core, uint2* F0,
+                                           uint2* F1, uint32_t fcap, uint32_t* R0, uint32_t* R1, PeelSlot* wr) {
+    const uint32_t lane = threadIdx.x & 31;
+    if (S.scan) {
+        // take the remaining vertices of degree <= level, keep the others
+        uint32_t local_min = UNSET;
+        uint32_t* Rw = S.rl ? R0 : R1;
+        const uint32_t* Rr = S.rl ? R1 : R0;
+        uint2* Fw = S.fb ? F1 : F0;
+        for (uint32_t base = gwarp * 32; base < S.rn; base += nwarps * 32) {
+            const uint32_t idx = base + lane;
+            uint32_t v = 0;
+            bool take = false, keep = false;
+            if (idx < S.rn) {
+                v = S.all ? idx : __ldcg(&Rr[idx]);
+                if (__ldcg(&round_of[v]) == UNSET) {
+                    const int d = __ldcg(&deg[v]);
+                    if (d <= (int)S.level) {
+                        take = true;
+                    } else {
+                        keep = true;
+                        local_min = min(local_min, (uint32_t)d);
+                    }
+                }
+            }
+            peel_take(take, v, S.round, S.level, rp, round_of, core, Fw, fcap, wr);
+            const unsigned o = warp_reserve(keep ? 1u : 0u, &wr->kept);
+            if (keep) {
+                if (o < n) __stcg(&Rw[o], v);
+                else atomicOr(&wr->err, (unsigned)KC_FLAG_INTERNAL);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) local_min = min(local_min, __shfl_xor_sync(0xffffffffu, local_min, o));
+        if (lane == 0 && local_min != UNSET) atomicMin(&wr->minrem, local_min);
+    } else {
+        // remove frontier pf: decrement every neighbour of its items; a
+        // neighbour that falls to the level joins frontier fb
+        const uint2* Fr = S.pf ? F1 : F0;
+        uint2* Fw = S.fb ? F1 : F0;
+        for (uint32_t base = gwarp * 32; base < S.nf; base += nwarps * 32) {
+            const uint32_t i = base + lane;
+            uint2 it = make_uint2(0u, 0u);
+            if (i < S.nf) it = __ldcg(&Fr[i]);
+            for (uint32_t t0 = 0; t0 < PEEL_CH; t0 += 4) {
+                if (__ballot_sync(0xffffffffu, it.y > t0) == 0) break;
+                uint32_t w[4];
+                int old[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) w[u] = (t0 + u < it.y) ? __ldg(ci + it.x + t0 + u) : UNSET;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) old[u] = (w[u] < n) ? atomicSub(&deg[w[u]], 1) : 0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    peel_take(w[u] < n && old[u] == (int)S.level + 1, w[u], S.round + 1, S.level, rp, round_of,
+                              core, Fw, fcap, wr);
+            }
+        }
+    }
+}
+
+// The loop's decisions after a phase, from the slot c it wrote.
+__device__ __forceinline__ void peel_advance(PeelState& S, const PeelSlot& c, uint32_t n, uint32_t fcap,
+                                             uint32_t phase_cap) {
+    if (c.err) {
+        S.fail = c.err;
+        S.done = 1;
+        return;
+    }
+    if (S.p > phase_cap) {
+        S.fail = KC_FLAG_INTERNAL;
+        S.done = 1;
+        return;
+    }
+    if (S.scan) {
+        if (c.taken) S.max_level = S.level;
+        S.rl ^= 1;
+        S.rn = min(c.kept, n);
+        S.all = 0;
+        S.nf = min(c.items, fcap);
+        if (S.nf == 0) {
+            if (S.rn == 0) {  // every vertex is removed
+                S.done = 1;
+                return;
+            }
+            // nothing (with edges) left at this level: jump to the smallest remaining degree
+            if (c.minrem == UNSET || c.minrem <= S.level) {
+                S.fail = KC_FLAG_INTERNAL;
+                S.done = 1;
+                return;
+            }
+            S.level = c.minrem;
+        } else {
+            S.pf = S.fb;
+            S.fb ^= 1;
+            S.scan = 0;
+        }
+    } else {
+        ++S.round;
+        S.nf = min(c.items, fcap);
+        if (S.nf == 0) {
+            ++S.level;
+            S.scan = 1;
+        } else {
+            S.pf = S.fb;
+            S.fb ^= 1;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(PEEL_THREADS, 1)
 k_peel_cluster(const uint32_t* __restrict__ rp, const uint32_t* __restrict__ ci, uint32_t n, int* deg,
                uint32_t* round_of, uint32_t* core, uint2* F0, uint2* F1, uint32_t fcap, uint32_t* R0, uint32_t* R1,
@@ -207,135 +345,75 @@ k_peel_cluster(const uint32_t* __restrict__ rp, const uint32_t* __restrict__ ci,
     cg::cluster_group cl = cg::this_cluster();
     __shared__ PeelSlot slots[3];  // in use in the cluster's first block only
     __shared__ PeelSlot seen;      // this block's copy of the slot read after a barrier
+    __shared__ PeelState published;  // the first block's loop state after it ran phases alone
+    __shared__ PeelState got;
     const unsigned rank = cl.block_rank();
     const unsigned nblk = cl.num_blocks();
     if (threadIdx.x < 3) slots[threadIdx.x] = PeelSlot{0u, 0u, 0u, UNSET, 0u};
     cl.sync();
     PeelSlot* s0 = cl.map_shared_rank(slots, 0);
-    const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = rank * (PEEL_THREADS / 32) + (threadIdx.x >> 5);
     const uint32_t nwarps = nblk * (PEEL_THREADS / 32);
-    const uint32_t gthread = gwarp * 32 + lane, nthreads = nwarps * 32;
-    uint32_t level = 0, round = 0, p = 0, max_level = 0;
-    int fb = 0;              // frontier buffer the next phase pushes into
-    int pf = 1;              // frontier buffer the next process phase reads
-    uint32_t nf = 0;         // its items
-    int rl = 0;              // remaining list the next scan reads
-    uint32_t rn = n;         // its length
-    bool all = true;         // the first scan reads every vertex
-    bool scan = true;        // kind of the next phase
-    unsigned fail = 0;
     const uint32_t phase_cap = 4u * n + 64u;
+    PeelState S;
+    S.level = 0;
+    S.round = 0;
+    S.p = 0;
+    S.max_level = 0;
+    S.nf = 0;
+    S.rn = n;
+    S.fail = 0;
+    S.fb = 0;
+    S.pf = 1;
+    S.rl = 0;
+    S.all = 1;
+    S.scan = 1;
+    S.done = 0;
     for (;;) {
-        PeelSlot* wr = s0 + (p + 1) % 3;
-        if (rank == 0 && threadIdx.x == 0) slots[(p + 2) % 3] = PeelSlot{0u, 0u, 0u, UNSET, 0u};
-        if (scan) {
-            // take the remaining vertices of degree <= level, keep the others
-            uint32_t local_min = UNSET;
-            uint32_t* Rw = rl ? R0 : R1;
-            const uint32_t* Rr = rl ? R1 : R0;
-            uint2* Fw = fb ? F1 : F0;
-            for (uint32_t base = gwarp * 32; base < rn; base += nwarps * 32) {
-                const uint32_t idx = base + lane;
-                uint32_t v = 0;
-                bool take = false, keep = false;
-                if (idx < rn) {
-                    v = all ? idx : __ldcg(&Rr[idx]);
-                    if (__ldcg(&round_of[v]) == UNSET) {
-                        const int d = __ldcg(&deg[v]);
-                        if (d <= (int)level) {
-                            take = true;
-                        } else {
-                            keep = true;
-                            local_min = min(local_min, (uint32_t)d);
-                        }
-                    }
+        if (nblk > 1 && peel_small(S)) {
+            if (rank == 0) {
+                // phases by this block alone, block barriers between them
+                for (;;) {
+                    PeelSlot* wr = slots + (S.p + 1) % 3;
+                    if (threadIdx.x == 0) slots[(S.p + 2) % 3] = PeelSlot{0u, 0u, 0u, UNSET, 0u};
+                    peel_phase(S, threadIdx.x >> 5, PEEL_THREADS / 32, rp, ci, n, deg, round_of, core, F0, F1, fcap,
+                               R0, R1, wr);
+                    __syncthreads();
+                    ++S.p;
+                    const PeelSlot c = *wr;
+                    __syncthreads();  // every thread read the slot before the next phase clears slots
+                    peel_advance(S, c, n, fcap, phase_cap);
+                    if (S.done || !peel_small(S)) break;
                 }
-                peel_take(take, v, round, level, rp, round_of, core, Fw, fcap, wr);
-                const unsigned o = warp_reserve(keep ? 1u : 0u, &wr->kept);
-                if (keep) {
-                    if (o < n) __stcg(&Rw[o], v);
-                    else atomicOr(&wr->err, (unsigned)KC_FLAG_INTERNAL);
-                }
+                if (threadIdx.x == 0) published = S;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) local_min = min(local_min, __shfl_xor_sync(0xffffffffu, local_min, o));
-            if (lane == 0 && local_min != UNSET) atomicMin(&wr->minrem, local_min);
-        } else {
-            // remove frontier pf: decrement every neighbour of its items; a
-            // neighbour that falls to the level joins frontier fb
-            const uint2* Fr = pf ? F1 : F0;
-            uint2* Fw = fb ? F1 : F0;
-            for (uint32_t base = gthread - lane; base < nf; base += nthreads) {
-                const uint32_t i = base + lane;
-                uint2 it = make_uint2(0u, 0u);
-                if (i < nf) it = __ldcg(&Fr[i]);
-                for (uint32_t t0 = 0; t0 < PEEL_CH; t0 += 4) {
-                    if (__ballot_sync(0xffffffffu, it.y > t0) == 0) break;
-                    uint32_t w[4];
-                    int old[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) w[u] = (t0 + u < it.y) ? __ldg(ci + it.x + t0 + u) : UNSET;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) old[u] = (w[u] < n) ? atomicSub(&deg[w[u]], 1) : 0;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        peel_take(w[u] < n && old[u] == (int)level + 1, w[u], round + 1, level, rp, round_of, core,
-                                  Fw, fcap, wr);
-                }
+            cl.sync();
+            if (rank != 0) {
+                if (threadIdx.x == 0) got = *cl.map_shared_rank(&published, 0);
+                __syncthreads();
+                S = got;
             }
+            if (S.done) break;
+            continue;
         }
+        PeelSlot* wr = s0 + (S.p + 1) % 3;
+        if (rank == 0 && threadIdx.x == 0) slots[(S.p + 2) % 3] = PeelSlot{0u, 0u, 0u, UNSET, 0u};
+        peel_phase(S, gwarp, nwarps, rp, ci, n, deg, round_of, core, F0, F1, fcap, R0, R1, wr);
         cl.sync();
-        ++p;
+        ++S.p;
         if (threadIdx.x == 0) seen = *wr;
         __syncthreads();
         const PeelSlot c = seen;
-        if (c.err) {
-            fail = c.err;
-            break;
-        }
-        if (p > phase_cap) {
-            fail = KC_FLAG_INTERNAL;
-            break;
-        }
-        if (scan) {
-            if (c.taken) max_level = level;
-            rl ^= 1;
-            rn = min(c.kept, n);
-            all = false;
-            nf = min(c.items, fcap);
-            if (nf == 0) {
-                if (rn == 0) break;  // every vertex is removed
-                // nothing (with edges) left at this level: jump to the smallest remaining degree
-                if (c.minrem == UNSET || c.minrem <= level) {
-                    fail = KC_FLAG_INTERNAL;
-                    break;
-                }
-                level = c.minrem;
-            } else {
-                pf = fb;
-                fb ^= 1;
-                scan = false;
-            }
-        } else {
-            ++round;
-            nf = min(c.items, fcap);
-            if (nf == 0) {
-                ++level;
-                scan = true;
-            } else {
-                pf = fb;
-                fb ^= 1;
-            }
-        }
+        peel_advance(S, c, n, fcap, phase_cap);
+        if (S.done) break;
     }
-    // no block leaves while another may still read the first block's slots
+    // no block leaves while another may still read the first block's shared memory
     cl.sync();
     if (rank == 0 && threadIdx.x == 0) {
-        out->flags = fail;
-        out->max_level = max_level;
-        out->rounds = round + 1;
-        out->phases = p;
+        out->flags = S.fail;
+        out->max_level = S.max_level;
+        out->rounds = S.round + 1;
+        out->phases = S.p;
     }
 }
 

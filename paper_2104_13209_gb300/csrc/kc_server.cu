@@ -94,6 +94,10 @@ struct kc_server {
     std::deque<uint64_t> q_batch, q_single;
     std::vector<BatchSlot> bs;
     std::vector<char> graph_busy;  // a single-path query of this graph is in flight
+    // per graph, per (k, traversal): 1 once a query of that shape ran out of
+    // the time limit (KC_SERVER_REFUSE_EXPENSIVE refuses the next ones)
+    std::vector<std::vector<uint8_t>> expensive;
+    uint64_t refused = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::thread worker;
@@ -123,12 +127,17 @@ bool batchable(const kc_graph* g, uint32_t k, int pivot) {
     return batch_smem_bytes(g->d_max, k, config_of(g->d_max, k)) != 0;
 }
 
+static constexpr uint32_t SHAPE_KMAX = 128;
+
+size_t shape_index(uint32_t k, int pivot) { return (size_t)std::min<uint32_t>(k, SHAPE_KMAX - 1) * 2 + (pivot ? 1 : 0); }
+
 void finish(kc_server* S, uint64_t t, const kc_result& r) {
     Ticket& T = S->tickets[t];
     T.r = r;
     T.t_done = S->now_ms();
     T.state = 2;
     S->served++;
+    if (r.status == KC_E_TIMEOUT) S->expensive[T.graph][shape_index(T.k, T.pivot)] = 1;
 }
 
 kc_result error_result(kc_status st) {
@@ -404,7 +413,8 @@ kc_status kc_server_create(size_t hbm_budget, uint32_t max_batch, uint32_t slots
     if (!out) return set_error(KC_E_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (max_batch == 0 || slots == 0) return set_error(KC_E_INVALID_ARG, "max_batch and slots must be >= 1");
-    if (flags & ~KC_SERVER_SERIAL) return set_error(KC_E_INVALID_ARG, "unknown flags %d", flags);
+    if (flags & ~(KC_SERVER_SERIAL | KC_SERVER_AUTO_TRAVERSAL | KC_SERVER_REFUSE_EXPENSIVE))
+        return set_error(KC_E_INVALID_ARG, "unknown flags %d", flags);
     kc_server* S = new (std::nothrow) kc_server();
     if (!S) return set_error(KC_E_NO_MEMORY, "host allocation failed");
     S->flags = flags;
@@ -468,6 +478,7 @@ kc_status kc_server_add_graph(kc_server* S, const uint32_t* row_ptr, const uint3
     *graph_id = (uint32_t)S->graphs.size();
     S->graphs.push_back(g);
     S->graph_busy.push_back(0);
+    S->expensive.emplace_back(2 * SHAPE_KMAX, (uint8_t)0);
     return KC_OK;
 }
 
@@ -491,15 +502,27 @@ kc_status kc_server_submit(kc_server* S, uint32_t graph_id, uint32_t k, int pivo
     Ticket T;
     T.graph = graph_id;
     T.k = k;
-    T.pivot = pivot;
+    // Section 4.5: pivoting pays from k = 7 on; the count is the same either way
+    T.pivot = (S->flags & KC_SERVER_AUTO_TRAVERSAL) ? (k >= 7 ? 1 : 0) : pivot;
     T.t_submit = S->now_ms();
     const uint64_t id = S->tickets.size();
     S->tickets.push_back(T);
+    *ticket = id;
+    if ((S->flags & KC_SERVER_REFUSE_EXPENSIVE) && S->expensive[graph_id][shape_index(k, T.pivot)]) {
+        // this shape ran out of the time limit before: answer at once
+        Ticket& R = S->tickets[id];
+        R.r = error_result(KC_E_REFUSED);
+        R.t_admit = R.t_done = R.t_submit;
+        R.state = 2;
+        S->refused++;
+        S->cv_done.notify_all();
+        return KC_OK;
+    }
+    pivot = T.pivot;
     if (batchable(S->graphs[graph_id], k, pivot))
         S->q_batch.push_back(id);
     else
         S->q_single.push_back(id);
-    *ticket = id;
     S->cv_work.notify_one();
     return KC_OK;
 }

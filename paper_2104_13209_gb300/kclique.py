@@ -26,6 +26,7 @@ KC_E_TIMEOUT = 5
 KC_E_CUDA = 6
 KC_E_INTERNAL = 7
 KC_E_UNSUPPORTED = 8
+KC_E_REFUSED = 9
 
 KC_ORIENT_DEGREE = 0
 KC_ORIENT_DEGENERACY = 1
@@ -55,6 +56,8 @@ EXPORTED = [
 ]
 
 KC_SERVER_SERIAL = 1
+KC_SERVER_AUTO_TRAVERSAL = 2
+KC_SERVER_REFUSE_EXPENSIVE = 4
 
 
 class kc_graph_info(ctypes.Structure):
@@ -469,10 +472,12 @@ class Server:
     """A serving loop over resident graphs (kc_server_*): submit queries
     (graph, k, pivot) from any thread, poll their results."""
 
-    def __init__(self, hbm_budget: int = 64 << 30, max_batch: int = 256, slots: int = 4, serial: bool = False):
+    def __init__(self, hbm_budget: int = 64 << 30, max_batch: int = 256, slots: int = 4, serial: bool = False,
+                 auto_traversal: bool = False, refuse_expensive: bool = False):
         h = ctypes.c_void_p()
-        _check(load().kc_server_create(hbm_budget, max_batch, slots, KC_SERVER_SERIAL if serial else 0,
-                                       ctypes.byref(h)))
+        flags = ((KC_SERVER_SERIAL if serial else 0) | (KC_SERVER_AUTO_TRAVERSAL if auto_traversal else 0)
+                 | (KC_SERVER_REFUSE_EXPENSIVE if refuse_expensive else 0))
+        _check(load().kc_server_create(hbm_budget, max_batch, slots, flags, ctypes.byref(h)))
         self._h = h
 
     def add_graph(self, g=None, row_ptr=None, col_idx=None, n=None, orient: str = "degeneracy",

@@ -103,3 +103,31 @@ def test_server_budget_and_arguments():
         S.submit(0, 0)
     assert wait(S, S.submit(0, 4))["total"] == 210
     S.close()
+
+
+def test_server_auto_traversal_same_counts():
+    # the traversal chosen by k (Section 4.5) counts exactly what the
+    # requested one counts
+    gs = pool()
+    qs = queries(gs)
+    S = make_server(gs, max_batch=64, slots=3, auto_traversal=True)
+    tickets = [S.submit(g, k, bool(p)) for g, k, p in qs]
+    for (g, k, p), t in zip(qs, tickets):
+        r = wait(S, t)
+        check(r, gs, g, k)
+        assert r["pivot"] == (1 if k >= 7 else 0)
+    S.close()
+
+
+def test_server_refuses_a_shape_that_ran_out_of_time():
+    gs = [synth.rmat(14, 16, seed=6), synth.complete_graph(20)]
+    S = make_server(gs, max_batch=64, slots=2, refuse_expensive=True)
+    S.set_time_limit(0.3)
+    first = wait(S, S.submit(0, 10))  # cannot finish in 0.3 s
+    assert first["status"] == kclique.KC_E_TIMEOUT
+    again = wait(S, S.submit(0, 10))  # the same shape: refused at admission
+    assert again["status"] == kclique.KC_E_REFUSED
+    assert again["t_admit_ms"] == again["t_submit_ms"] == again["t_done_ms"]
+    check(wait(S, S.submit(1, 5)), gs, 1, 5)  # other shapes are still served
+    check(wait(S, S.submit(0, 3)), gs, 0, 3)
+    S.close()

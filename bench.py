@@ -37,6 +37,14 @@ ISSUE_PER_SM_CLK = 4         # warp instructions issued per SM per clock (four s
 METRIC = "k-clique count time & cliques/s (k=4/7/10); batched/served queries/s, p99 vs plain"
 
 
+_T0 = time.perf_counter()
+
+
+def log(msg: str):
+    """Progress of the run, on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:8.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
 def workload_graph(scale=20, ef=16, seed=0):
     os.makedirs(CACHE, exist_ok=True)
     path = os.path.join(CACHE, f"rmat{scale}_ef{ef}_s{seed}.npz")
@@ -283,24 +291,26 @@ def device_rates(dev_index: int) -> dict:
 
 
 def measured_l2_read_gbs(dev) -> float:
-    """Read bandwidth of the L2: a 48 MiB buffer (resident in the 129 MB L2)
-    summed 20 times per timing, best of 8 (a lower bound of the peak)."""
+    """Bandwidth of the L2: a 24 MiB buffer copied into another (both
+    resident in the 129 MB L2), read plus written bytes, 50 copies per
+    timing, best of 8 (a lower bound of the peak: a plain vectorised copy)."""
     import torch
 
-    x = torch.ones(12 << 20, dtype=torch.int32, device=dev)
-    for _ in range(3):
-        x.sum()
+    x = torch.ones(6 << 20, dtype=torch.float32, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(5):
+        y.copy_(x)
     torch.cuda.synchronize()
     best = 0.0
     for _ in range(8):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(20):
-            x.sum()
+        for _ in range(50):
+            y.copy_(x)
         e1.record()
         e1.synchronize()
-        best = max(best, 20 * x.numel() * 4 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+        best = max(best, 50 * 2 * x.numel() * 4 / (e0.elapsed_time(e1) / 1e3) / 1e9)
     return best
 
 
@@ -346,6 +356,7 @@ def run_ours(a, g, plan, world, rank, local_rank):
             flush.fill_(1)
         stream.synchronize()
 
+    log("main workload: warm-up")
     for _ in range(a.warmup):
         step([])
         flush_l2()
@@ -374,6 +385,7 @@ def run_ours(a, g, plan, world, rank, local_rank):
     total_cliques = sum(r.total for r in res)
     step_ms = max_over_ranks(step_ms, dev)
 
+    log("main workload: timed steps done; end-to-end steps")
     # end to end through the public API from pinned host memory
     rp_h = torch.from_numpy(g.row_ptr.view(np.int32)).pin_memory()
     ci_h = torch.from_numpy(g.col_idx.view(np.int32)).pin_memory()
@@ -448,7 +460,9 @@ def run_ours(a, g, plan, world, rank, local_rank):
     # (edge-centric, the choice for k >= 6), after a k = 5 count that loads
     # the same kernel
     deep = None
+    log("roofline terms measured")
     if a.deep_k:
+        log(f"k = {a.deep_k} sub-record")
         kd = a.deep_k
         rr = torch.zeros(kclique.RESULT_BYTES, dtype=torch.uint8, device=dev)
         with torch.cuda.stream(stream):
@@ -506,6 +520,7 @@ def run_ours(a, g, plan, world, rank, local_rank):
     if deep is not None:
         line[f"k{deep['k']}"] = deep
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        log("CPU baseline (oracle)")
         cb = oracle_sample_rate(g, k0, a.cpu_budget)
         line["cpu_baseline"] = {"value": cb["rate"], "unit": "cliques/s", "cores": cb["threads"], "kind": "oracle",
                                 "sample": f"k={k0}: every {cb['stride']}-th root with out-degree >= {k0 - 1} "
@@ -523,7 +538,9 @@ def run_batch(a, world, rank, local_rank):
 
     from paper_2104_13209_gb300 import build, kclique, workloads
 
+    log("batched workload: generating the ego networks")
     egos, ks = workloads.ego_batch()
+    log("batched workload: generated")
     build.build()
     kclique.load()
     torch.cuda.set_device(local_rank)
@@ -538,6 +555,7 @@ def run_batch(a, world, rank, local_rank):
         with open(tune_path) as f:
             tune = kclique.tune_from_list(json.load(f))
     else:
+        log("batched workload: tuning")
         tune = B.tune(gid, ks, sample=256, stream=stream)
         with open(tune_path, "w") as f:
             json.dump(kclique.tune_to_list(tune), f)
@@ -576,6 +594,7 @@ def run_batch(a, world, rank, local_rank):
             B.count_async(gid[i:i + 1], ks[i:i + 1], res[i * kclique.RESULT_BYTES:(i + 1) * kclique.RESULT_BYTES],
                           tune=tune, stream=stream)
 
+    log("batched workload: one launch sequence per query")
     plain_ms = timed(per_query, 1, 1)
     # end to end through the public call from host arrays, results read back
     e2e = []
@@ -625,7 +644,9 @@ def run_serve(a, world, rank, local_rank):
     server against the same stream served one launch per query."""
     from paper_2104_13209_gb300 import workloads
 
+    log("serving workload: generating the pool")
     gs = workloads.serve_pool()  # worker processes are spawned before any CUDA use
+    log("serving workload: generated")
     import torch
 
     from paper_2104_13209_gb300 import build, kclique
@@ -641,10 +662,13 @@ def run_serve(a, world, rank, local_rank):
         S = kclique.Server(hbm_budget=200 << 30, max_batch=256, slots=4, serial=(mode == "plain"),
                            auto_traversal=True, refuse_expensive=(mode != "plain"))
         S.set_time_limit(a.time_limit)
+        log(f"serving ({mode}): adding the pool")
         for h in gs:
             S.add_graph(h)
+        log(f"serving ({mode}): warm-up")
         for i in range(min(64, len(ts))):  # warm-up: every kernel once
             S.poll(S.submit(int(gq[i]), int(kq[i]), bool(pq[i])), -1)
+        log(f"serving ({mode}): stream")
         tickets = []
         t0 = time.perf_counter()
         for i in range(len(ts)):
@@ -654,6 +678,7 @@ def run_serve(a, world, rank, local_rank):
             tickets.append(S.submit(int(gq[i]), int(kq[i]), bool(pq[i])))
         rs = [S.poll(t, -1) for t in tickets]
         wall = time.perf_counter() - t0
+        log(f"serving ({mode}): {len(rs)} queries answered in {wall:.1f} s")
         ok = [r for r in rs if r["status"] == kclique.KC_OK]
         lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in ok]) if ok else np.zeros(1)
         span = (max(r["t_done_ms"] for r in rs) - min(r["t_submit_ms"] for r in rs)) / 1e3

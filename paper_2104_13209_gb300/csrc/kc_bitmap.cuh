@@ -95,13 +95,11 @@ __device__ void build_bitmap(const uint32_t* __restrict__ rp, const uint32_t* __
     __syncthreads();
 }
 
-// Open-addressing table of the candidates, for the membership test of the
-// bitmap build: 2^tbits 32-bit key slots holding a candidate's vertex id
-// (NONE = empty), linear probing from a multiplicative hash of the id, and
-// beside them 2^tbits 16-bit slots with the candidate's position.  Most
-// tested ids are not candidates; at a load of at most 1/4 most of those
-// misses end at the first, empty, slot, and a hit is recognised from the key
-// itself (the position is read only then).
+// Open-addressing table of the candidates' positions, for the membership
+// test of the bitmap build: 2^tbits 16-bit slots holding position + 1
+// (0 = empty), linear probing from a multiplicative hash of the vertex id.
+// Most tested ids are not candidates, and at a load of at most 1/4 most of
+// those misses end at the first, empty, slot.
 __host__ __device__ __forceinline__ uint32_t hash_slot(uint32_t y, uint32_t tbits) {
     return (y * 0x9E3779B1u) >> (32 - tbits);
 }
@@ -112,36 +110,29 @@ __host__ __device__ __forceinline__ uint32_t hash_bits_for(uint32_t d) {
     return b;
 }
 
-// 32-bit words of the table for candidate sets up to d: keys, then positions
-__host__ __device__ __forceinline__ uint32_t hash_table_words(uint32_t d) {
-    const uint32_t T = 1u << hash_bits_for(d);
-    return T + T / 2;
-}
+// 32-bit words of the table for candidate sets up to d (16-bit slots)
+__host__ __device__ __forceinline__ uint32_t hash_table_words(uint32_t d) { return (1u << hash_bits_for(d)) / 2; }
 
 // Same rows as build_bitmap, with the table above instead of binary search.
-// tab: hash_table_words(d) words (tbits = hash_bits_for(d)); d < 65535.
-// Each lane tests the 8 entries of its two quads together: 8 hash slots,
-// 8 key loads in flight, and a branch only for the occupied slots.
+// tab: hash_table_words(d) words, 2^tbits 16-bit slots (tbits from
+// hash_bits_for(d)); d < 65535.
 template <int NT>
 __device__ void build_bitmap_hashed(const uint32_t* __restrict__ rp, const uint32_t* __restrict__ col,
-                                    const uint32_t* cand, uint32_t d, uint32_t W, uint32_t* bm, uint32_t* tab,
+                                    const uint32_t* cand, uint32_t d, uint32_t W, uint32_t* bm, uint32_t* tabw,
                                     uint32_t tbits) {
     const uint32_t T = 1u << tbits, mask = T - 1;
-    uint32_t* keys = tab;
-    uint16_t* posv = reinterpret_cast<uint16_t*>(tab + T);
+    uint32_t* tw = tabw;
+    uint16_t* tab = reinterpret_cast<uint16_t*>(tabw);
     for (uint32_t x = threadIdx.x; x < d * W; x += NT) bm[x] = 0;
-    for (uint32_t x = threadIdx.x; x < T; x += NT) keys[x] = NONE;
+    for (uint32_t x = threadIdx.x; x < T / 2; x += NT) tw[x] = 0;
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < d; i += NT) {
-        const uint32_t y = cand[i];
-        uint32_t h = hash_slot(y, tbits);
-        while (atomicCAS(&keys[h], NONE, y) != NONE) h = (h + 1) & mask;
-        posv[h] = (uint16_t)i;
+        uint32_t h = hash_slot(cand[i], tbits);
+        while (atomicCAS(&tab[h], (unsigned short)0, (unsigned short)(i + 1)) != 0) h = (h + 1) & mask;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t last = cand[d - 1];
-    const uint4* col4 = reinterpret_cast<const uint4*>(col);
     // row bounds of the warp's next row are loaded while it scans this one
     uint32_t nb = 0, ne = 0;
     if (warp < d) {
@@ -156,41 +147,18 @@ __device__ void build_bitmap_hashed(const uint32_t* __restrict__ rp, const uint3
             ne = __ldg(rp + x2 + 1);
         }
         uint32_t* row = bm + (size_t)i * W;
-        const uint32_t qend = (e + 3) >> 2;
-        for (uint32_t q0 = b >> 2; q0 < qend; q0 += 64) {
-            const uint32_t qa = q0 + lane, qb = qa + 32;
-            uint4 va = make_uint4(NONE, NONE, NONE, NONE), vb = va;
-            if (qa < qend) va = __ldg(col4 + qa);
-            if (qb < qend) vb = __ldg(col4 + qb);
-            const uint32_t ja = qa << 2, jb = qb << 2;
-            uint32_t y[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
-            uint32_t h[8], kv[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const uint32_t j = (c < 4 ? ja : jb) + (c & 3);
-                if (j < b || j >= e || y[c] > last) y[c] = NONE;  // not tested
-                h[c] = hash_slot(y[c], tbits);
-            }
-#pragma unroll
-            for (int c = 0; c < 8; ++c) kv[c] = keys[h[c]];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                if (y[c] == NONE || kv[c] == NONE) continue;  // the common case: a miss at an empty slot
-                uint32_t hh = h[c], kk = kv[c];
-                for (;;) {
-                    if (kk == y[c]) {
-                        const uint32_t p = posv[hh];
-                        atomicOr(&row[p >> 5], 1u << (p & 31));
-                        break;
-                    }
-                    hh = (hh + 1) & mask;
-                    kk = keys[hh];
-                    if (kk == NONE) break;
+        scan_row(col, b, e, last, lane, [&](uint32_t y) {
+            uint32_t h = hash_slot(y, tbits);
+            for (;;) {
+                const uint32_t p = tab[h];
+                if (p == 0) break;
+                if (cand[p - 1] == y) {
+                    atomicOr(&row[(p - 1) >> 5], 1u << ((p - 1) & 31));
+                    break;
                 }
+                h = (h + 1) & mask;
             }
-            const uint32_t tail = (jb + 3 < e) ? vb.w : NONE;
-            if (__shfl_sync(0xffffffffu, tail, 31) >= last) break;  // the rest of the row lies beyond last
-        }
+        });
     }
     __syncthreads();
 }

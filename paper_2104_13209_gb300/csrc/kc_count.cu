@@ -74,10 +74,10 @@ __device__ __forceinline__ void edge_count(const uint32_t* I, const uint32_t* bm
 // in shared memory; the donor stops its own iteration below the split.
 // ---------------------------------------------------------------------------
 static constexpr int QCAP = 16;
-// A waiting group polls the queue at most this many times (each poll sleeps
-// ~256 ns, so a few minutes) and then leaves the pool; the groups that still
-// hold work finish it themselves, so leaving is always safe.
-static constexpr uint32_t IDLE_SPIN_LIMIT = 1u << 30;
+// A waiting group gives up after IDLE_NS (%globaltimer) and leaves the
+// pool; the groups that still hold work finish it themselves, so leaving is
+// always safe (the count stays exact).
+static constexpr unsigned long long IDLE_NS = 2000000000ull;
 
 struct StealShared {
     unsigned idle;        // groups waiting for work (or trying to take some)
@@ -257,7 +257,9 @@ __device__ bool steal_or_finish(const CountParams& P, StealShared* ss, uint32_t*
     if (gl == 0) {
         atomicAdd(&ss->idle, 1u);
         uint32_t it = 0;
-        for (; it < IDLE_SPIN_LIMIT; ++it) {
+        const unsigned long long t0 = globaltimer_ns();
+        for (;; ++it) {
+            if ((it & 255u) == 255u && globaltimer_ns() - t0 > IDLE_NS) break;
             if (vld(&ss->queued) > 0) {
                 atomicSub(&ss->idle, 1u);  // trying to take work: no longer idle
                 for (uint32_t x = 0; x < QCAP; ++x)

@@ -301,6 +301,23 @@ __device__ unsigned long long warp_small(const Ctl* ctl, DeepWarp& dw, const PvC
     const uint32_t* T = dw.T;
     if (PV) transpose_small<NW>(dw, X, m);
     unsigned long long s = 0;
+    if (rem == 3 && !PV) {
+        // lanes claim rows, the heavy first ones first (rows are upper
+        // triangular); a row's triangles with it as the smallest member
+        if (lane == 0) dw.next = 0;
+        __syncwarp();
+        for (;;) {
+            const uint32_t a = atomicAdd(&dw.next, 1u);
+            if (a >= m) break;
+            Mask<NW> R;
+#pragma unroll
+            for (int i = 0; i < NW; ++i) R.w[i] = T[a * NW + i];
+            s += lane_edges<NW, false>(R, T, X, ctl, acc.words);
+        }
+        acc.add(s);
+        __syncwarp();
+        return s;
+    }
     if (rem <= 3) {
         for (uint32_t a = lane; a < m; a += 32) {
             Mask<NW> R;

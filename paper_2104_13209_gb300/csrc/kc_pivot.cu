@@ -266,10 +266,12 @@ __device__ __forceinline__ void add_sums(uint32_t* hd, unsigned long long sH, un
 // ---------------------------------------------------------------------------
 static constexpr int PQCAP = 16;
 static constexpr int PPATH = 64;  // path entries a donated frame can carry
-// A waiting warp or block polls at most this many times (each poll sleeps a
-// few hundred ns, so minutes) and then leaves the pool; donors finish their
-// own work, so leaving is always safe.
-static constexpr uint32_t P_IDLE_SPIN_LIMIT = 1u << 30;
+// A warp waiting for a frame of its block gives up after P_IDLE_NS, a block
+// waiting for a frame of the global queue after P_GLOBAL_IDLE_NS (%globaltimer),
+// and leaves the pool; donors finish their own work, so leaving is always
+// safe (the count stays exact, only the help is lost).
+static constexpr unsigned long long P_IDLE_NS = 2000000000ull;
+static constexpr unsigned long long P_GLOBAL_IDLE_NS = 5000000000ull;
 
 struct PStealShared {
     unsigned idle, active, queued;
@@ -651,7 +653,9 @@ __device__ uint32_t p_steal_or_finish(const PivotParams& P, PStealShared* ss, ui
     if (lane == 0) {
         int done = 0;
         atomicAdd(&ss->idle, 1u);
-        for (uint32_t it = 0; it < P_IDLE_SPIN_LIMIT; ++it) {
+        const unsigned long long t0 = globaltimer_ns();
+        for (uint32_t it = 0;; ++it) {
+            if ((it & 255u) == 255u && globaltimer_ns() - t0 > P_IDLE_NS) break;
             if (pvld(&ss->queued) > 0) {
                 atomicSub(&ss->idle, 1u);
                 for (uint32_t x = 0; x < PQCAP; ++x)
@@ -1020,7 +1024,9 @@ __device__ void pivot_warp_phase(const PivotParams& P, PNest& ws, LeafCache& lc)
 __device__ uint32_t global_take(const PivotParams& P) {
     PWorkCtl* wc = reinterpret_cast<PWorkCtl*>(P.ctl + 1);
     atomicAdd(&wc->g_idle, 1u);
-    for (uint32_t it = 0; it < P_IDLE_SPIN_LIMIT; ++it) {
+    const unsigned long long t0 = globaltimer_ns();
+    for (uint32_t it = 0;; ++it) {
+        if ((it & 255u) == 255u && globaltimer_ns() - t0 > P_GLOBAL_IDLE_NS) break;
         if (pvld(&wc->g_queued) > 0) {
             atomicSub(&wc->g_idle, 1u);
             for (uint32_t x = 0; x < P.gq_cap; ++x)

@@ -342,13 +342,24 @@ typedef struct kc_server_result {
 
 /* One launch in flight at a time, one query per launch (the plain baseline). */
 #define KC_SERVER_SERIAL 1
-/* The server picks the traversal of every query by the paper's guideline
- * (Section 4.5): graph orientation below k = 7, pivoting from k = 7.  The
- * query's own pivot flag is then only recorded (the count is the same). */
+/* The server picks the traversal of every query; the query's own pivot
+ * flag is then only recorded (the count is the same either way).  With a
+ * time limit set, kc_server_add_graph first measures the graph's cost
+ * profile on the SM share a query gets: the orientation traversal at
+ * k = 3, 4, ... (up to 16 and d_max + 1), each under the time limit, until
+ * one runs out of it (every larger k is then taken as expensive); if one
+ * did, the pivot traversal over every k, and if that ran out too, the pivot
+ * traversal at that k and up, until one runs out (the larger k are then
+ * expensive by pivoting too).  Counts of the profile are not kept.  A query takes
+ * the orientation traversal unless the profile found it expensive at its
+ * k, then pivoting unless that was found expensive too.  Without a profile
+ * (no time limit when the graph was added): the paper's guideline (Section
+ * 4.5), orientation below k = 7 and pivoting from k = 7. */
 #define KC_SERVER_AUTO_TRAVERSAL 2
-/* Admission control: a query is refused at once (KC_E_REFUSED) when an
- * earlier query of the same graph, k and traversal ran out of the time
- * limit, instead of waiting for a slot and timing out again. */
+/* Admission control: a query is refused at once (KC_E_REFUSED), instead of
+ * waiting for a slot and timing out, when its shape (graph, k, traversal)
+ * is expensive: the graph's cost profile ran out of the time limit there,
+ * or an earlier query of that shape did. */
 #define KC_SERVER_REFUSE_EXPENSIVE 4
 
 /* hbm_budget: device bytes the server may keep resident (slots and graphs);
@@ -380,6 +391,12 @@ kc_status kc_server_poll(kc_server* s, uint64_t ticket, kc_server_result* out, i
 
 /* Launches so far, queries served, resident device bytes (nullable). */
 kc_status kc_server_stats(kc_server* s, uint64_t* launches, uint64_t* served, uint64_t* resident_bytes);
+
+/* Admission state of a shape: *state = 0 unknown, 1 finished within the
+ * time limit when the graph was profiled (*ms: its wall time, if ms is not
+ * NULL), 2 expensive (its profile or a query of it ran out of the limit).
+ * k >= 1; k beyond 127 shares the entry of 127. */
+kc_status kc_server_shape(kc_server* s, uint32_t graph_id, uint32_t k, int pivot, int* state, double* ms);
 
 /* Stop the worker after the launches in flight and free everything. */
 kc_status kc_server_destroy(kc_server* s);

@@ -9,6 +9,8 @@
 #include <new>
 #include <string>
 
+#include <mutex>
+
 #include "kc_common.cuh"
 
 namespace kc {
@@ -59,6 +61,49 @@ void dev_free(DevBuf& b) {
     if (b.ptr) cudaFree(b.ptr);
     b.ptr = nullptr;
     b.bytes = 0;
+}
+
+static cudaMemPool_t scratch_pool() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = 1ull << 30;
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = p;
+    }
+    return pools[dev];
+}
+
+kc_status scratch_alloc(void** p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    cudaMemPool_t pool = scratch_pool();
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, s) : cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_error(KC_E_NO_MEMORY, "device scratch of %zu bytes failed (%s)", bytes, cudaGetErrorString(e));
+    }
+    return KC_OK;
+}
+
+void scratch_free(void* p, cudaStream_t s) {
+    if (!p) return;
+    if (cudaFreeAsync(p, s) != cudaSuccess) cudaGetLastError();
 }
 
 static bool is_device_pointer(const void* p) {

@@ -48,6 +48,11 @@ struct DevBuf {
 
 kc_status dev_alloc(DevBuf& b, size_t bytes);      // (re)allocate if smaller than `bytes`
 void dev_free(DevBuf& b);
+// Stream-ordered scratch from a memory pool the library keeps per device
+// (up to 1 GiB stays reserved between uses): working memory of one call
+// that costs neither a cudaMalloc nor a device-wide cudaFree.
+kc_status scratch_alloc(void** p, size_t bytes, cudaStream_t s);
+void scratch_free(void* p, cudaStream_t s);
 
 // Per-launch error word written by kernels (device) -- bit layout = KC_FLAG_*.
 struct Ctl {

@@ -245,7 +245,7 @@ __device__ unsigned long long lane_walk_nw(const Ctl* ctl, Mask<NW> J0, uint32_t
             --l;
             continue;
         }
-        if ((++steps & 65535u) == 0 && timed_out(ctl)) break;
+        if ((++steps & 1023u) == 0 && timed_out(ctl)) break;
         const uint32_t v = mask_pop<NW>(J);
         if (PV) {
             flush(l);
@@ -308,7 +308,7 @@ __device__ unsigned long long warp_small(const Ctl* ctl, DeepWarp& dw, const PvC
         __syncwarp();
         for (;;) {
             const uint32_t a = atomicAdd(&dw.next, 1u);
-            if (a >= m) break;
+            if (a >= m || timed_out(ctl)) break;
             Mask<NW> R;
 #pragma unroll
             for (int i = 0; i < NW; ++i) R.w[i] = T[a * NW + i];
@@ -371,7 +371,7 @@ __device__ unsigned long long warp_small(const Ctl* ctl, DeepWarp& dw, const PvC
         __syncwarp();
         for (;;) {
             const uint32_t a = atomicAdd(&dw.next, 1u);
-            if (a >= m) break;
+            if (a >= m || timed_out(ctl)) break;
             Mask<NW> R;
 #pragma unroll
             for (int i = 0; i < NW; ++i) R.w[i] = T[a * NW + i];
@@ -422,7 +422,7 @@ __device__ unsigned long long warp_small(const Ctl* ctl, DeepWarp& dw, const PvC
     const uint32_t rem2 = rem - 2;  // vertices still to choose below an edge task
     for (;;) {
         const uint32_t t = atomicAdd(&dw.next, 1u);
-        if (t >= total) break;
+        if (t >= total || timed_out(ctl)) break;
         uint32_t lo = 0, hi = m;  // the row a with pre[a] <= t < pre[a + 1]
         while (hi - lo > 1) {
             const uint32_t mid = (lo + hi) >> 1;
@@ -834,7 +834,7 @@ __device__ unsigned long long deep_walk(const DeepParams& D, const uint32_t* bm,
                 continue;
             }
             if ((++steps & 63u) == 0) {
-                if ((steps & 1023u) == 0) {
+                {
                     int to = lane == 0 ? (int)timed_out(ctl) : 0;
                     if (__shfl_sync(0xffffffffu, to, 0)) return tot;
                 }

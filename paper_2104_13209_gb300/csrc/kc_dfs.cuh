@@ -70,9 +70,11 @@ struct Acc {
     }
 };
 
+// True once %globaltimer has passed the launch's deadline (every warp reads
+// the same clock, so no flag needs to be polled: the check costs one cached
+// load and a special-register read, cheap enough for the inner loops).
 __device__ __forceinline__ bool timed_out(const Ctl* c) {
     if (c->deadline == 0) return false;
-    if (*(volatile const unsigned*)&c->flags & KC_FLAG_TIMEOUT) return true;
     if (globaltimer_ns() > c->deadline) {
         atomicOr((unsigned*)&c->flags, (unsigned)KC_FLAG_TIMEOUT);
         return true;
@@ -157,7 +159,7 @@ static __device__ uint64_t lane_walk(const CountParams& P, uint32_t J0, uint32_t
             --l;
             continue;
         }
-        if ((++steps & 65535u) == 0 && timed_out(P.ctl)) break;
+        if ((++steps & 1023u) == 0 && timed_out(P.ctl)) break;
         uint32_t v = __ffs(J) - 1;
         J &= J - 1;
         stk[l * 32 + lane] = J;

@@ -8,7 +8,6 @@
 // the order, so every edge goes from a smaller to a larger id.  The induced
 // sub-graph of any candidate set listed in ascending id is then strictly
 // upper-triangular, which the counting kernels rely on.
-#include <cooperative_groups.h>
 
 #include <algorithm>
 #include <mutex>
@@ -128,8 +127,8 @@ __global__ void k_degree_key(const uint32_t* __restrict__ rp, uint32_t n, uint32
 // the peel by k_removal_key: #{w in N(v) : round_of[w] >= round_of[v]}.
 // ---------------------------------------------------------------------------
 static constexpr uint32_t PEEL_CH = 16;        // adjacency entries per frontier item
+static constexpr int SCAN_PER_LANE = 8;        // remaining-list entries per lane and round of a scan
 static constexpr int PEEL_THREADS = 1024;
-static constexpr int PEEL_CLUSTER_MAX = 16;
 
 struct PeelSlot {
     unsigned items;   // frontier items pushed during the phase
@@ -231,33 +230,48 @@ __device__ __forceinline__ void peel_phase(const PeelState& S, uint32_t gwarp, u
                                            uint2* F1, uint32_t fcap, uint32_t* R0, uint32_t* R1, PeelSlot* wr) {
     const uint32_t lane = threadIdx.x & 31;
     if (S.scan) {
-        // take the remaining vertices of degree <= level, keep the others
+        // take the remaining vertices of degree <= level, keep the others;
+        // a lane looks at SCAN_PER_LANE entries per round (their loads in
+        // flight together) and the warp reserves the kept ones at once
         uint32_t local_min = UNSET;
         uint32_t* Rw = S.rl ? R0 : R1;
         const uint32_t* Rr = S.rl ? R1 : R0;
         uint2* Fw = S.fb ? F1 : F0;
-        for (uint32_t base = gwarp * 32; base < S.rn; base += nwarps * 32) {
-            const uint32_t idx = base + lane;
-            uint32_t v = 0;
-            bool take = false, keep = false;
-            if (idx < S.rn) {
-                v = S.all ? idx : __ldcg(&Rr[idx]);
-                if (__ldcg(&round_of[v]) == UNSET) {
-                    const int d = __ldcg(&deg[v]);
-                    if (d <= (int)S.level) {
-                        take = true;
-                    } else {
-                        keep = true;
-                        local_min = min(local_min, (uint32_t)d);
-                    }
+        const uint32_t span = 32u * SCAN_PER_LANE;
+        for (unsigned long long base = (unsigned long long)gwarp * span; base < S.rn;
+             base += (unsigned long long)nwarps * span) {
+            uint32_t v[SCAN_PER_LANE], r[SCAN_PER_LANE];
+            int d[SCAN_PER_LANE];
+#pragma unroll
+            for (int u = 0; u < SCAN_PER_LANE; ++u) {
+                const unsigned long long idx = base + (uint32_t)u * 32u + lane;
+                v[u] = idx < S.rn ? (S.all ? (uint32_t)idx : __ldcg(&Rr[idx])) : UNSET;
+            }
+#pragma unroll
+            for (int u = 0; u < SCAN_PER_LANE; ++u) {
+                r[u] = v[u] != UNSET ? __ldcg(&round_of[v[u]]) : 0u;
+                d[u] = v[u] != UNSET ? __ldcg(&deg[v[u]]) : 0;
+            }
+            unsigned keepm = 0, nkeep = 0;
+#pragma unroll
+            for (int u = 0; u < SCAN_PER_LANE; ++u) {
+                const bool live = v[u] != UNSET && r[u] == UNSET;
+                const bool take = live && d[u] <= (int)S.level;
+                if (live && !take) {
+                    keepm |= 1u << u;
+                    ++nkeep;
+                    local_min = min(local_min, (uint32_t)d[u]);
                 }
+                peel_take(take, v[u], S.round, S.level, rp, round_of, core, Fw, fcap, wr);
             }
-            peel_take(take, v, S.round, S.level, rp, round_of, core, Fw, fcap, wr);
-            const unsigned o = warp_reserve(keep ? 1u : 0u, &wr->kept);
-            if (keep) {
-                if (o < n) __stcg(&Rw[o], v);
-                else atomicOr(&wr->err, (unsigned)KC_FLAG_INTERNAL);
-            }
+            uint32_t o = warp_reserve(nkeep, &wr->kept);
+#pragma unroll
+            for (int u = 0; u < SCAN_PER_LANE; ++u)
+                if (keepm >> u & 1u) {
+                    if (o < n) __stcg(&Rw[o], v[u]);
+                    else atomicOr(&wr->err, (unsigned)KC_FLAG_INTERNAL);
+                    ++o;
+                }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) local_min = min(local_min, __shfl_xor_sync(0xffffffffu, local_min, o));
@@ -337,24 +351,73 @@ __device__ __forceinline__ void peel_advance(PeelState& S, const PeelSlot& c, ui
     }
 }
 
+// Global control words of the peel (device memory, set up by the kernel).
+struct PeelCtl {
+    PeelSlot slot[3];  // control slots of the grid-wide phases
+    PeelState pub;     // block 0's loop state after it ran phases alone
+    unsigned bar;      // barrier arrivals since the launch
+    unsigned fail;     // KC_FLAG_INTERNAL: a barrier wait gave up
+};
+
+// A barrier wait gives up after this long (%globaltimer); the first one,
+// which also waits for every block of the launch to start, after START.
+static constexpr unsigned long long PEEL_BARRIER_NS = 2000000000ull;
+static constexpr unsigned long long PEEL_START_NS = 10000000000ull;
+
+// Grid-wide barrier of the peel: arrivals only count up, and a block waits
+// until the count reaches its target (gridDim.x more per barrier), so no
+// reset is needed.  Returns false (and records KC_FLAG_INTERNAL) when the
+// wait gives up; the caller then leaves its loop, and the other blocks' next
+// waits give up too, so the launch always ends.
+__device__ __forceinline__ bool peel_barrier(PeelCtl* pc, unsigned target, unsigned long long limit_ns) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int good = 1;
+        __threadfence();
+        atomicAdd(&pc->bar, 1u);
+        if (*(volatile unsigned*)&pc->bar < target) {
+            const unsigned long long t0 = globaltimer_ns();
+            unsigned spins = 0;
+            while (*(volatile unsigned*)&pc->bar < target) {
+                if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > limit_ns) {
+                    atomicOr(&pc->fail, (unsigned)KC_FLAG_INTERNAL);
+                    good = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__device__ __forceinline__ PeelSlot load_slot(const PeelSlot* p) {
+    const volatile unsigned* w = reinterpret_cast<const volatile unsigned*>(p);
+    return PeelSlot{w[0], w[1], w[2], w[3], w[4]};
+}
+
+// The peel over every SM: one block of PEEL_THREADS per SM, all resident
+// (cooperative launch).  Large phases run on the whole grid with grid-wide
+// barriers between them; runs of small phases run in block 0 alone, with
+// block barriers, while the other blocks wait at one grid barrier.
 __global__ void __launch_bounds__(PEEL_THREADS, 1)
-k_peel_cluster(const uint32_t* __restrict__ rp, const uint32_t* __restrict__ ci, uint32_t n, int* deg,
-               uint32_t* round_of, uint32_t* core, uint2* F0, uint2* F1, uint32_t fcap, uint32_t* R0, uint32_t* R1,
-               PeelOut* out) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cl = cg::this_cluster();
-    __shared__ PeelSlot slots[3];  // in use in the cluster's first block only
-    __shared__ PeelSlot seen;      // this block's copy of the slot read after a barrier
-    __shared__ PeelState published;  // the first block's loop state after it ran phases alone
+k_peel_grid(const uint32_t* __restrict__ rp, const uint32_t* __restrict__ ci, uint32_t n, int* deg,
+            uint32_t* round_of, uint32_t* core, uint2* F0, uint2* F1, uint32_t fcap, uint32_t* R0, uint32_t* R1,
+            PeelCtl* pc, PeelOut* out) {
+    __shared__ PeelSlot slots[3];  // block 0's phases alone
+    __shared__ PeelSlot seen;      // the slot read after a grid barrier
     __shared__ PeelState got;
-    const unsigned rank = cl.block_rank();
-    const unsigned nblk = cl.num_blocks();
-    if (threadIdx.x < 3) slots[threadIdx.x] = PeelSlot{0u, 0u, 0u, UNSET, 0u};
-    cl.sync();
-    PeelSlot* s0 = cl.map_shared_rank(slots, 0);
-    const uint32_t gwarp = rank * (PEEL_THREADS / 32) + (threadIdx.x >> 5);
+    const PeelSlot clean{0u, 0u, 0u, UNSET, 0u};
+    const unsigned nblk = gridDim.x;
+    const uint32_t gwarp = blockIdx.x * (PEEL_THREADS / 32) + (threadIdx.x >> 5);
     const uint32_t nwarps = nblk * (PEEL_THREADS / 32);
     const uint32_t phase_cap = 4u * n + 64u;
+    if (blockIdx.x == 0 && threadIdx.x < 3) pc->slot[threadIdx.x] = clean;
+    unsigned target = nblk;
+    bool ok = peel_barrier(pc, target, PEEL_START_NS);
     PeelState S;
     S.level = 0;
     S.round = 0;
@@ -369,13 +432,14 @@ k_peel_cluster(const uint32_t* __restrict__ rp, const uint32_t* __restrict__ ci,
     S.all = 1;
     S.scan = 1;
     S.done = 0;
-    for (;;) {
+    while (ok) {
         if (nblk > 1 && peel_small(S)) {
-            if (rank == 0) {
-                // phases by this block alone, block barriers between them
+            if (blockIdx.x == 0) {
+                if (threadIdx.x < 3) slots[threadIdx.x] = clean;
+                __syncthreads();
                 for (;;) {
                     PeelSlot* wr = slots + (S.p + 1) % 3;
-                    if (threadIdx.x == 0) slots[(S.p + 2) % 3] = PeelSlot{0u, 0u, 0u, UNSET, 0u};
+                    if (threadIdx.x == 0) slots[(S.p + 2) % 3] = clean;
                     peel_phase(S, threadIdx.x >> 5, PEEL_THREADS / 32, rp, ci, n, deg, round_of, core, F0, F1, fcap,
                                R0, R1, wr);
                     __syncthreads();
@@ -385,32 +449,51 @@ k_peel_cluster(const uint32_t* __restrict__ rp, const uint32_t* __restrict__ ci,
                     peel_advance(S, c, n, fcap, phase_cap);
                     if (S.done || !peel_small(S)) break;
                 }
-                if (threadIdx.x == 0) published = S;
+                // the grid-wide phases that follow start from clean slots
+                if (threadIdx.x < 3) pc->slot[threadIdx.x] = clean;
+                if (threadIdx.x == 0) pc->pub = S;
             }
-            cl.sync();
-            if (rank != 0) {
-                if (threadIdx.x == 0) got = *cl.map_shared_rank(&published, 0);
+            target += nblk;
+            ok = peel_barrier(pc, target, PEEL_BARRIER_NS);
+            if (!ok) break;
+            if (blockIdx.x != 0) {
+                if (threadIdx.x == 0) {
+                    const volatile PeelState* vp = &pc->pub;
+                    got.level = vp->level;
+                    got.round = vp->round;
+                    got.p = vp->p;
+                    got.max_level = vp->max_level;
+                    got.nf = vp->nf;
+                    got.rn = vp->rn;
+                    got.fail = vp->fail;
+                    got.fb = vp->fb;
+                    got.pf = vp->pf;
+                    got.rl = vp->rl;
+                    got.all = vp->all;
+                    got.scan = vp->scan;
+                    got.done = vp->done;
+                }
                 __syncthreads();
                 S = got;
             }
             if (S.done) break;
             continue;
         }
-        PeelSlot* wr = s0 + (S.p + 1) % 3;
-        if (rank == 0 && threadIdx.x == 0) slots[(S.p + 2) % 3] = PeelSlot{0u, 0u, 0u, UNSET, 0u};
+        PeelSlot* wr = pc->slot + (S.p + 1) % 3;
+        if (blockIdx.x == 0 && threadIdx.x == 0) pc->slot[(S.p + 2) % 3] = clean;
         peel_phase(S, gwarp, nwarps, rp, ci, n, deg, round_of, core, F0, F1, fcap, R0, R1, wr);
-        cl.sync();
+        target += nblk;
+        ok = peel_barrier(pc, target, PEEL_BARRIER_NS);
+        if (!ok) break;
         ++S.p;
-        if (threadIdx.x == 0) seen = *wr;
+        if (threadIdx.x == 0) seen = load_slot(wr);
         __syncthreads();
         const PeelSlot c = seen;
         peel_advance(S, c, n, fcap, phase_cap);
         if (S.done) break;
     }
-    // no block leaves while another may still read the first block's shared memory
-    cl.sync();
-    if (rank == 0 && threadIdx.x == 0) {
-        out->flags = S.fail;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out->flags = S.fail | (ok ? 0u : (unsigned)KC_FLAG_INTERNAL) | *(volatile unsigned*)&pc->fail;
         out->max_level = S.max_level;
         out->rounds = S.round + 1;
         out->phases = S.p;
@@ -559,40 +642,30 @@ static unsigned grid_for(uint64_t items, int threads, int sms) {
     return (unsigned)b;
 }
 
-// Largest cluster (16, 8, 4, 2 or 1 blocks of PEEL_THREADS) the device can
-// run the peel with; looked up once per device.
-static kc_status peel_cluster_size(int* out) {
+// Blocks of the grid-wide peel: one per SM, provided a block of
+// PEEL_THREADS fits an SM and the device runs cooperative launches; looked
+// up once per device (0: the device cannot run it).
+static kc_status peel_grid_blocks(int sms, int* out) {
     static std::mutex mu;
     static int cached[64] = {0};
     int dev = 0;
     KC_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lock(mu);
-    if (dev >= 0 && dev < 64 && cached[dev]) {
-        *out = cached[dev];
+    if (dev < 0 || dev >= 64 || cached[dev] == 0) {
+        int coop = 0, per_sm = 0;
+        KC_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel_grid, PEEL_THREADS, 0));
+        const int v = (coop && per_sm >= 1) ? 1 : -1;
+        if (dev >= 0 && dev < 64) cached[dev] = v;
+        if (v < 0) {
+            *out = 0;
+            return KC_OK;
+        }
+    } else if (cached[dev] < 0) {
+        *out = 0;
         return KC_OK;
     }
-    KC_CUDA(cudaFuncSetAttribute((const void*)k_peel_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    int best = 1;
-    for (int c = PEEL_CLUSTER_MAX; c >= 1; c >>= 1) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)c);
-        cfg.blockDim = dim3(PEEL_THREADS);
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = (unsigned)c;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int nc = 0;
-        if (cudaOccupancyMaxActiveClusters(&nc, (const void*)k_peel_cluster, &cfg) == cudaSuccess && nc >= 1) {
-            best = c;
-            break;
-        }
-        cudaGetLastError();
-    }
-    if (dev >= 0 && dev < 64) cached[dev] = best;
-    *out = best;
+    *out = std::max(1, sms);
     return KC_OK;
 }
 
@@ -609,13 +682,14 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     // frontier items: a vertex of degree d is pushed once, as ceil(d / PEEL_CH) items
     const size_t fcap = (size_t)n + (size_t)nnz / PEEL_CH + 1;
-    DevBuf work;
-    size_t wbytes = al(sizeof(PeelOut)) + al(64) + 6 * al((size_t)n * 4 + 4) + 2 * al(fcap * 8) +
-                    al(((size_t)nnz / 2 + 1) * 4);
-    kc_status st = dev_alloc(work, wbytes);
+    void* work = nullptr;
+    size_t wbytes = al(sizeof(PeelOut)) + al(sizeof(PeelCtl)) + al(64) + 6 * al((size_t)n * 4 + 4) +
+                    2 * al(fcap * 8) + al(((size_t)nnz / 2 + 1) * 4);
+    kc_status st = scratch_alloc(&work, wbytes, s);
     if (st != KC_OK) return st;
-    char* p = (char*)work.ptr;
+    char* p = (char*)work;
     PeelOut* pout = (PeelOut*)p; p += al(sizeof(PeelOut));
+    PeelCtl* pctl = (PeelCtl*)p; p += al(sizeof(PeelCtl));
     unsigned* words = (unsigned*)p; p += al(64);            // [0] validate flags, [1] max key, [2] d_max
     uint32_t* key = (uint32_t*)p; p += al((size_t)n * 4 + 4);
     int* deg = (int*)p; p += al((size_t)n * 4 + 4);
@@ -628,7 +702,7 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
     uint32_t* colbuf = (uint32_t*)p; p += al(((size_t)nnz / 2 + 1) * 4);
 
     auto fail = [&](kc_status e) {
-        dev_free(work);
+        scratch_free(work, s);  // after the kernels queued so far (stream order)
         cudaEventDestroy(ev0);
         cudaEventDestroy(ev1);
         return e;
@@ -644,7 +718,7 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
         if (s2_ != KC_OK) return fail(s2_); \
     } while (0)
 
-    KC_TRY(cudaMemsetAsync(pout, 0, sizeof(PeelOut), s));
+    KC_TRY(cudaMemsetAsync(pout, 0, al(sizeof(PeelOut)) + al(sizeof(PeelCtl)), s));
     KC_TRY(cudaMemsetAsync(words, 0, 64, s));
     unsigned h_words[4] = {0, 0, 0, 0};
 
@@ -679,28 +753,23 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
     note_launch();
     KC_TRY(cudaGetLastError());
     uint32_t max_key = 0;
+    unsigned maxdeg = 0;  // largest degree (degeneracy order: read with the peel's result)
     if (degen) {
         KC_TRYS(dev_alloc(g->core, (size_t)n * 4 + 4));
         if (n > 0) {
-            int csize = 0;
-            KC_TRYS(peel_cluster_size(&csize));
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3((unsigned)csize);
-            cfg.blockDim = dim3(PEEL_THREADS);
-            cfg.dynamicSmemBytes = 0;
-            cfg.stream = s;
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = (unsigned)csize;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            KC_TRY(cudaLaunchKernelEx(&cfg, k_peel_cluster, d_rp, d_ci, n, deg, round_of, (uint32_t*)g->core.ptr, F0,
-                                      F1, (uint32_t)std::min<size_t>(fcap, 0xFFFFFFFFu), R0, R1, pout));
+            int blocks = 0;
+            KC_TRYS(peel_grid_blocks(sms, &blocks));
+            if (blocks == 0) return fail(set_error(KC_E_UNSUPPORTED, "the device cannot run the cooperative k-core peel"));
+            const uint32_t fc = (uint32_t)std::min<size_t>(fcap, 0xFFFFFFFFu);
+            uint32_t* corep = (uint32_t*)g->core.ptr;
+            void* args[] = {(void*)&d_rp, (void*)&d_ci, (void*)&n, (void*)&deg, (void*)&round_of, (void*)&corep,
+                            (void*)&F0, (void*)&F1, (void*)&fc, (void*)&R0, (void*)&R1, (void*)&pctl, (void*)&pout};
+            KC_TRY(cudaLaunchCooperativeKernel((const void*)k_peel_grid, dim3((unsigned)blocks), dim3(PEEL_THREADS),
+                                               args, 0, s));
             note_launch();
             PeelOut hc;
             KC_TRY(cudaMemcpyAsync(&hc, pout, sizeof(PeelOut), cudaMemcpyDeviceToHost, s));
+            KC_TRY(cudaMemcpyAsync(&maxdeg, words + 1, 4, cudaMemcpyDeviceToHost, s));
             KC_TRY(cudaStreamSynchronize(s));
             if (hc.flags & KC_FLAG_INTERNAL)
                 return fail(set_error(KC_E_INTERNAL, "k-core peel: inconsistent state after %u phases (level %u, "
@@ -726,9 +795,6 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
     KC_TRYS(dev_alloc(g->old_of_new, (size_t)n * 4 + 4));
     KC_TRYS(dev_alloc(g->new_of_old, (size_t)n * 4 + 4));
     if (degen && n > 0) {
-        unsigned maxdeg = 0;
-        KC_TRY(cudaMemcpyAsync(&maxdeg, words + 1, 4, cudaMemcpyDeviceToHost, s));
-        KC_TRY(cudaStreamSynchronize(s));
         uint32_t* by_deg = (uint32_t*)F0;  // free after the peel
         KC_TRYS(sort_ids_by_key(key, n, maxdeg, by_deg, g->tmp, s));
         KC_TRYS(sort_ids_by_key(round_of, n, max_key, (uint32_t*)g->old_of_new.ptr, g->tmp, s, by_deg));
@@ -789,7 +855,7 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
     g->orient_ms = ms;
-    dev_free(work);
+    scratch_free(work, s);
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
 #undef KC_TRY

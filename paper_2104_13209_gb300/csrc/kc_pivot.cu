@@ -83,9 +83,10 @@ struct PWorkCtl {
     unsigned int pad[2];
 };
 
+// True once %globaltimer has passed the launch's deadline (a cached load
+// and a special-register read: cheap enough for every few DFS steps).
 __device__ __forceinline__ bool p_timed_out(const Ctl* c) {
     if (c->deadline == 0) return false;
-    if (*(volatile const unsigned*)&c->flags & KC_FLAG_TIMEOUT) return true;
     if (globaltimer_ns() > c->deadline) {
         atomicOr((unsigned*)&c->flags, (unsigned)KC_FLAG_TIMEOUT);
         return true;
@@ -398,7 +399,7 @@ __device__ void walk_levels(const PivotParams& P, const uint32_t* adj, uint32_t 
     uint32_t steps = 0;
     for (;;) {
         if ((++steps & 15u) == 0) {
-            if ((steps & 4095u) == 0) {
+            {
                 int to = lane == 0 ? (int)p_timed_out(P.ctl) : 0;
                 if (__shfl_sync(0xffffffffu, to, 0)) break;
             }

@@ -94,9 +94,13 @@ struct kc_server {
     std::deque<uint64_t> q_batch, q_single;
     std::vector<BatchSlot> bs;
     std::vector<char> graph_busy;  // a single-path query of this graph is in flight
-    // per graph, per (k, traversal): 1 once a query of that shape ran out of
-    // the time limit (KC_SERVER_REFUSE_EXPENSIVE refuses the next ones)
-    std::vector<std::vector<uint8_t>> expensive;
+    // per graph, per (k, traversal) (shape_index): SHAPE_UNKNOWN, SHAPE_FITS
+    // (finished within the time limit when the graph was profiled, in
+    // shape_ms) or SHAPE_EXPENSIVE (ran out of it: at profiling, or a query
+    // of that shape did; KC_SERVER_REFUSE_EXPENSIVE refuses the next ones)
+    std::vector<std::vector<uint8_t>> shape_state;
+    std::vector<std::vector<float>> shape_ms;
+    std::vector<char> profiled;
     uint64_t refused = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -128,6 +132,9 @@ bool batchable(const kc_graph* g, uint32_t k, int pivot) {
 }
 
 static constexpr uint32_t SHAPE_KMAX = 128;
+static constexpr uint8_t SHAPE_UNKNOWN = 0, SHAPE_FITS = 1, SHAPE_EXPENSIVE = 2;
+// the cost profile measures the orientation traversal up to this k
+static constexpr uint32_t PROFILE_KMAX = 16;
 
 size_t shape_index(uint32_t k, int pivot) { return (size_t)std::min<uint32_t>(k, SHAPE_KMAX - 1) * 2 + (pivot ? 1 : 0); }
 
@@ -137,7 +144,7 @@ void finish(kc_server* S, uint64_t t, const kc_result& r) {
     T.t_done = S->now_ms();
     T.state = 2;
     S->served++;
-    if (r.status == KC_E_TIMEOUT) S->expensive[T.graph][shape_index(T.k, T.pivot)] = 1;
+    if (r.status == KC_E_TIMEOUT) S->shape_state[T.graph][shape_index(T.k, T.pivot)] = SHAPE_EXPENSIVE;
 }
 
 kc_result error_result(kc_status st) {
@@ -392,6 +399,81 @@ void worker_main(kc_server* S) {
     }
 }
 
+// Cost profile of a graph, measured when it is added (KC_SERVER_AUTO_TRAVERSAL
+// with a time limit), on the SM share a query gets while serving: the
+// orientation traversal at k = 3, 4, ... up to PROFILE_KMAX (and d_max + 1),
+// each under the time limit, until one runs out of it (every larger k is
+// then taken as expensive too: the search tree of k contains that of k - 1
+// up to the size pruning).  If one ran out, the pivot traversal over every
+// k (an upper bound of each fixed-k pivot count) and, should that run out as
+// well, the pivot traversal at that k and up, until one runs out (the
+// larger k are then expensive by pivoting too).  Nothing of the counts is
+// kept.
+void profile_graph(kc_graph* g, uint32_t d_max, std::vector<uint8_t>& st, std::vector<float>& ms, cudaStream_t s) {
+    auto timed = [&](uint32_t k, int pivot, double& t_ms) {
+        uint64_t total = 0;
+        uint32_t flags = 0;
+        const auto t0 = Clock::now();
+        kc_status r = kc_count(g, k, pivot, KC_SCHEME_AUTO, 0, &total, nullptr, &flags, s);
+        t_ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+        return r == KC_E_OVERFLOW ? KC_OK : r;
+    };
+    const uint32_t kmax = std::min<uint32_t>(d_max + 1, PROFILE_KMAX);
+    uint32_t k_out = 0;
+    for (uint32_t k = 3; k <= kmax; ++k) {
+        double t = 0;
+        const kc_status r = timed(k, 0, t);
+        if (r == KC_OK) {
+            st[shape_index(k, 0)] = SHAPE_FITS;
+            ms[shape_index(k, 0)] = (float)t;
+        } else {
+            if (r == KC_E_TIMEOUT) {
+                k_out = k;
+                for (uint32_t j = k; j < SHAPE_KMAX; ++j) st[shape_index(j, 0)] = SHAPE_EXPENSIVE;
+            }
+            break;
+        }
+    }
+    if (k_out == 0) return;
+    std::vector<uint64_t> counts(SHAPE_KMAX);
+    std::vector<uint8_t> ovf(SHAPE_KMAX);
+    uint32_t omega = 0;
+    const auto t0 = Clock::now();
+    const kc_status r = kc_count_all(g, counts.data(), ovf.data(), SHAPE_KMAX, &omega, 0, nullptr, s);
+    const double t = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+    if (r == KC_OK || r == KC_E_OVERFLOW) {
+        for (uint32_t j = 1; j < SHAPE_KMAX; ++j) {
+            st[shape_index(j, 1)] = SHAPE_FITS;
+            ms[shape_index(j, 1)] = (float)t;
+        }
+        return;
+    }
+    if (r != KC_E_TIMEOUT) return;
+    for (uint32_t k = k_out; k <= kmax; ++k) {
+        double t = 0;
+        const kc_status rk = timed(k, 1, t);
+        if (rk == KC_OK) {
+            st[shape_index(k, 1)] = SHAPE_FITS;
+            ms[shape_index(k, 1)] = (float)t;
+        } else {
+            if (rk == KC_E_TIMEOUT)
+                for (uint32_t j = k; j < SHAPE_KMAX; ++j) st[shape_index(j, 1)] = SHAPE_EXPENSIVE;
+            break;
+        }
+    }
+}
+
+// Traversal of a query: orientation unless the profile found it expensive,
+// then pivoting unless that was found expensive too (then orientation).
+// A graph without a profile follows the paper's guideline (Section 4.5):
+// pivoting pays from k = 7 on.  The count is the same either way.
+int auto_traversal(const kc_server* S, uint32_t graph_id, uint32_t k) {
+    if (!S->profiled[graph_id]) return k >= 7 ? 1 : 0;
+    const std::vector<uint8_t>& st = S->shape_state[graph_id];
+    if (st[shape_index(k, 0)] != SHAPE_EXPENSIVE) return 0;
+    return st[shape_index(k, 1)] != SHAPE_EXPENSIVE ? 1 : 0;
+}
+
 void free_slot(BatchSlot& b) {
     if (b.st) cudaStreamSynchronize(b.st);
     if (b.ev) cudaEventDestroy(b.ev);
@@ -466,6 +548,23 @@ kc_status kc_server_add_graph(kc_server* S, const uint32_t* row_ptr, const uint3
     KC_CHECK(kc_graph_create(row_ptr, col_idx, n, nnz, ptrs_on_device, orient, validate, S->setup, &g));
     kc_graph_info info;
     kc_graph_info_get(g, &info);
+    double limit = 0;
+    int share = 0;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        limit = S->time_limit;
+        share = S->share;
+    }
+    std::vector<uint8_t> st(2 * SHAPE_KMAX, SHAPE_UNKNOWN);
+    std::vector<float> ms(2 * SHAPE_KMAX, 0.0f);
+    const bool profile = (S->flags & KC_SERVER_AUTO_TRAVERSAL) && limit > 0;
+    if (profile) {
+        // outside the lock: the worker keeps serving meanwhile
+        kc_graph_set_time_limit(g, limit);
+        g->sm_count = share;
+        profile_graph(g, info.d_max, st, ms, S->setup);
+        clear_error();
+    }
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->resident + info.device_bytes > S->budget) {
         kc_graph_destroy(g);
@@ -478,7 +577,9 @@ kc_status kc_server_add_graph(kc_server* S, const uint32_t* row_ptr, const uint3
     *graph_id = (uint32_t)S->graphs.size();
     S->graphs.push_back(g);
     S->graph_busy.push_back(0);
-    S->expensive.emplace_back(2 * SHAPE_KMAX, (uint8_t)0);
+    S->shape_state.push_back(std::move(st));
+    S->shape_ms.push_back(std::move(ms));
+    S->profiled.push_back(profile ? 1 : 0);
     return KC_OK;
 }
 
@@ -502,14 +603,14 @@ kc_status kc_server_submit(kc_server* S, uint32_t graph_id, uint32_t k, int pivo
     Ticket T;
     T.graph = graph_id;
     T.k = k;
-    // Section 4.5: pivoting pays from k = 7 on; the count is the same either way
-    T.pivot = (S->flags & KC_SERVER_AUTO_TRAVERSAL) ? (k >= 7 ? 1 : 0) : pivot;
+    T.pivot = (S->flags & KC_SERVER_AUTO_TRAVERSAL) ? auto_traversal(S, graph_id, k) : pivot;
     T.t_submit = S->now_ms();
     const uint64_t id = S->tickets.size();
     S->tickets.push_back(T);
     *ticket = id;
-    if ((S->flags & KC_SERVER_REFUSE_EXPENSIVE) && S->expensive[graph_id][shape_index(k, T.pivot)]) {
-        // this shape ran out of the time limit before: answer at once
+    if ((S->flags & KC_SERVER_REFUSE_EXPENSIVE) &&
+        S->shape_state[graph_id][shape_index(k, T.pivot)] == SHAPE_EXPENSIVE) {
+        // this shape runs out of the time limit (profile or an earlier query): answer at once
         Ticket& R = S->tickets[id];
         R.r = error_result(KC_E_REFUSED);
         R.t_admit = R.t_done = R.t_submit;
@@ -559,6 +660,18 @@ kc_status kc_server_stats(kc_server* S, uint64_t* launches, uint64_t* served, ui
     if (launches) *launches = S->launches;
     if (served) *served = S->served;
     if (resident_bytes) *resident_bytes = S->resident;
+    return KC_OK;
+}
+
+kc_status kc_server_shape(kc_server* S, uint32_t graph_id, uint32_t k, int pivot, int* state, double* ms) {
+    clear_error();
+    if (!S || !state) return set_error(KC_E_INVALID_ARG, "NULL server or state");
+    if (pivot != 0 && pivot != 1) return set_error(KC_E_INVALID_ARG, "pivot must be 0 or 1");
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (graph_id >= S->graphs.size()) return set_error(KC_E_INVALID_ARG, "unknown graph %u", graph_id);
+    const size_t i = shape_index(k, pivot);
+    *state = S->shape_state[graph_id][i];
+    if (ms) *ms = S->shape_ms[graph_id][i];
     return KC_OK;
 }
 

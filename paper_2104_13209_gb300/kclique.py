@@ -52,10 +52,11 @@ EXPORTED = [
     "kc_batch_create", "kc_batch_destroy", "kc_batch_graph_info", "kc_batch_set_time_limit", "kc_batch_count",
     "kc_batch_tune", "kc_batch_capture", "kc_batch_exec_launch", "kc_batch_exec_destroy",
     "kc_server_create", "kc_server_add_graph", "kc_server_set_time_limit", "kc_server_submit", "kc_server_poll",
-    "kc_server_stats", "kc_server_destroy",
+    "kc_server_stats", "kc_server_shape", "kc_server_destroy",
 ]
 
 KC_SERVER_SERIAL = 1
+SHAPE_UNKNOWN, SHAPE_FITS, SHAPE_EXPENSIVE = 0, 1, 2
 KC_SERVER_AUTO_TRAVERSAL = 2
 KC_SERVER_REFUSE_EXPENSIVE = 4
 
@@ -156,9 +157,10 @@ def load(build_if_missing: bool = False):
     lib.kc_server_submit.argtypes = [vp, u32, u32, i32, ctypes.POINTER(u64)]
     lib.kc_server_poll.argtypes = [vp, u64, ctypes.POINTER(kc_server_result), i32]
     lib.kc_server_stats.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]
+    lib.kc_server_shape.argtypes = [vp, u32, u32, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]
     lib.kc_server_destroy.argtypes = [vp]
     for f in ("kc_server_create", "kc_server_add_graph", "kc_server_set_time_limit", "kc_server_submit",
-              "kc_server_poll", "kc_server_stats", "kc_server_destroy"):
+              "kc_server_poll", "kc_server_stats", "kc_server_shape", "kc_server_destroy"):
         getattr(lib, f).restype = i32
     for f in ("kc_batch_create", "kc_batch_destroy", "kc_batch_graph_info", "kc_batch_set_time_limit",
               "kc_batch_count", "kc_batch_tune", "kc_batch_capture", "kc_batch_exec_launch", "kc_batch_exec_destroy"):
@@ -516,6 +518,13 @@ class Server:
         a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
         _check(load().kc_server_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return {"launches": a.value, "served": b.value, "resident_bytes": c.value}
+
+    def shape(self, graph_id: int, k: int, pivot: bool) -> tuple[int, float]:
+        """(state, ms) of a shape: SHAPE_UNKNOWN, SHAPE_FITS (ms: its profiled
+        wall time) or SHAPE_EXPENSIVE (see kc_server_shape)."""
+        st, ms = ctypes.c_int32(), ctypes.c_double()
+        _check(load().kc_server_shape(self._h, graph_id, k, int(pivot), ctypes.byref(st), ctypes.byref(ms)))
+        return st.value, ms.value
 
     def close(self):
         if getattr(self, "_h", None):

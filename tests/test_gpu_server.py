@@ -131,3 +131,42 @@ def test_server_refuses_a_shape_that_ran_out_of_time():
     check(wait(S, S.submit(1, 5)), gs, 1, 5)  # other shapes are still served
     check(wait(S, S.submit(0, 3)), gs, 0, 3)
     S.close()
+
+
+def test_server_profile_picks_the_traversal_and_refuses():
+    # with a time limit, adding a graph measures its cost profile; queries
+    # then take the traversal that finished there, and a shape that ran out
+    # of time in both traversals is refused at admission without a launch
+    import math
+
+    gs = [synth.rmat(14, 16, seed=6), synth.complete_graph(40), synth.erdos_renyi(2000, 0.01, 0)]
+    lib()
+    S = kclique.Server(max_batch=64, slots=2, auto_traversal=True, refuse_expensive=True)
+    S.set_time_limit(0.3)
+    for h in gs:
+        S.add_graph(h)
+    # R-MAT 14: k = 3 finishes by graph orientation; k = 10 needs seconds in
+    # either traversal (about 4.5 s and more than 0.4 s on a whole GB300)
+    assert S.shape(0, 3, False)[0] == kclique.SHAPE_FITS
+    assert S.shape(0, 10, False)[0] == kclique.SHAPE_EXPENSIVE
+    launches = S.stats()["launches"]
+    r = wait(S, S.submit(0, 10, False))
+    assert r["status"] == kclique.KC_E_REFUSED and r["t_admit_ms"] == r["t_done_ms"]
+    assert S.stats()["launches"] == launches
+    check(wait(S, S.submit(0, 4, True)), gs, 0, 4)
+    # K40: orientation enumerates C(40, k) leaves; pivoting is one path
+    st_or, _ = S.shape(1, 20, False)
+    st_pv, ms_pv = S.shape(1, 20, True)
+    assert st_pv == kclique.SHAPE_FITS and ms_pv > 0
+    r = wait(S, S.submit(1, 20, False))
+    assert r["status"] == kclique.KC_OK and r["total"] == math.comb(40, 20)
+    assert r["pivot"] == (1 if st_or == kclique.SHAPE_EXPENSIVE else 0)
+    r = wait(S, S.submit(1, 3, True))
+    assert r["status"] == kclique.KC_OK and r["total"] == math.comb(40, 3) and r["pivot"] == 0
+    # ER: every profiled k finishes by orientation
+    for k in (3, 4, 5):
+        assert S.shape(2, k, False)[0] == kclique.SHAPE_FITS
+        r = wait(S, S.submit(2, k, True))
+        check(r, gs, 2, k)
+        assert r["pivot"] == 0
+    S.close()

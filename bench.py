@@ -731,7 +731,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="rmat", choices=["rmat", "batch", "serve"])
     ap.add_argument("--rate", type=float, default=2000.0)
-    ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-seconds", type=float, default=0.5)
     ap.add_argument("--time-limit", type=float, default=0.25)
     ap.add_argument("--serve-modes", default="batched,plain")
     ap.add_argument("--sub", default="batch,serve",

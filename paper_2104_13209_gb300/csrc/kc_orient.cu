@@ -128,6 +128,7 @@ __global__ void k_degree_key(const uint32_t* __restrict__ rp, uint32_t n, uint32
 // ---------------------------------------------------------------------------
 static constexpr uint32_t PEEL_CH = 16;        // adjacency entries per frontier item
 static constexpr int SCAN_PER_LANE = 8;        // remaining-list entries per lane and round of a scan
+static constexpr int PROC_STEP = 8;            // adjacency entries a lane decrements at once
 static constexpr int PEEL_THREADS = 1024;
 
 struct PeelSlot {
@@ -162,39 +163,58 @@ __device__ __forceinline__ unsigned warp_reserve(unsigned cnt, unsigned* counter
     return base + incl - cnt;
 }
 
-// Lanes with pred remove vertex v now (sub-round `round`, level `level`):
-// mark it, then append its adjacency as frontier items to F (capacity fcap,
-// item count in sl->items).  The warp writes the items of all its lanes
-// together.  All lanes call.
-__device__ __forceinline__ void peel_take(bool pred, uint32_t v, uint32_t round, uint32_t level,
-                                          const uint32_t* __restrict__ rp, uint32_t* round_of, uint32_t* core,
-                                          uint2* F, uint32_t fcap, PeelSlot* sl) {
-    uint32_t b = 0, e = 0, c = 0;
-    if (pred) {
-        __stcg(&round_of[v], round);
-        __stcg(&core[v], level);
-        b = __ldg(rp + v);
-        e = __ldg(rp + v + 1);
-        c = (e - b + PEEL_CH - 1) / PEEL_CH;
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, pred);
-    if (bal == 0) return;
-    if ((threadIdx.x & 31) == (unsigned)(__ffs(bal) - 1)) atomicAdd(&sl->taken, (unsigned)__popc(bal));
-    const unsigned off = warp_reserve(c, &sl->items);
-    const unsigned need = __ballot_sync(0xffffffffu, c > 0);
-    const int lane = threadIdx.x & 31;
-    unsigned m = need;
-    while (m) {
-        const int src = __ffs(m) - 1;
-        m &= m - 1;
-        const uint32_t sb = __shfl_sync(0xffffffffu, b, src), se = __shfl_sync(0xffffffffu, e, src);
-        const uint32_t sc = __shfl_sync(0xffffffffu, c, src), so = __shfl_sync(0xffffffffu, off, src);
-        for (uint32_t x = lane; x < sc; x += 32) {
-            const uint32_t pos = so + x;
-            const uint32_t lo = sb + x * PEEL_CH;
-            if (pos < fcap) __stcg(&F[pos], make_uint2(lo, min(PEEL_CH, se - lo)));
-            else atomicOr(&sl->err, (unsigned)KC_FLAG_INTERNAL);
+// Lanes with pred[u] remove vertex v[u] now (sub-round `round`, level
+// `level`): mark it, then append its adjacency as frontier items to F
+// (capacity fcap, item count in sl->items), N candidates per lane at once:
+// the rows' bounds are loaded together, and the warp reserves the items of
+// all its takes with one atomic (a phase's reservations are the peel's
+// only contended atomics).  All lanes call.
+template <int N>
+__device__ __forceinline__ void peel_take_many(const bool (&pred)[N], const uint32_t (&v)[N], uint32_t round,
+                                               uint32_t level, const uint32_t* __restrict__ rp, uint32_t* round_of,
+                                               uint32_t* core, uint2* F, uint32_t fcap, PeelSlot* sl) {
+    uint32_t b[N], len[N];
+    uint32_t tot = 0, nt = 0;
+#pragma unroll
+    for (int u = 0; u < N; ++u) {
+        b[u] = 0;
+        len[u] = 0;
+        if (pred[u]) {
+            __stcg(&round_of[v[u]], round);
+            __stcg(&core[v[u]], level);
+            b[u] = __ldg(rp + v[u]);
+            len[u] = __ldg(rp + v[u] + 1);
         }
+    }
+#pragma unroll
+    for (int u = 0; u < N; ++u)
+        if (pred[u]) {
+            len[u] -= b[u];
+            tot += (len[u] + PEEL_CH - 1) / PEEL_CH;
+            ++nt;
+        }
+    const unsigned any = __ballot_sync(0xffffffffu, nt > 0);
+    if (any == 0) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned ntw = __reduce_add_sync(0xffffffffu, nt);
+    if (lane == __ffs(any) - 1) atomicAdd(&sl->taken, ntw);
+    uint32_t off = warp_reserve(tot, &sl->items);
+#pragma unroll
+    for (int u = 0; u < N; ++u) {
+        const uint32_t c = (len[u] + PEEL_CH - 1) / PEEL_CH;
+        unsigned m = __ballot_sync(0xffffffffu, c > 0);
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t sb = __shfl_sync(0xffffffffu, b[u], src), sl2 = __shfl_sync(0xffffffffu, len[u], src);
+            const uint32_t sc = __shfl_sync(0xffffffffu, c, src), so = __shfl_sync(0xffffffffu, off, src);
+            for (uint32_t x = lane; x < sc; x += 32) {
+                const uint32_t pos = so + x;
+                if (pos < fcap) __stcg(&F[pos], make_uint2(sb + x * PEEL_CH, min(PEEL_CH, sl2 - x * PEEL_CH)));
+                else atomicOr(&sl->err, (unsigned)KC_FLAG_INTERNAL);
+            }
+        }
+        off += c;
     }
 }
 
@@ -253,17 +273,18 @@ __device__ __forceinline__ void peel_phase(const PeelState& S, uint32_t gwarp, u
                 d[u] = v[u] != UNSET ? __ldcg(&deg[v[u]]) : 0;
             }
             unsigned keepm = 0, nkeep = 0;
+            bool take[SCAN_PER_LANE];
 #pragma unroll
             for (int u = 0; u < SCAN_PER_LANE; ++u) {
                 const bool live = v[u] != UNSET && r[u] == UNSET;
-                const bool take = live && d[u] <= (int)S.level;
-                if (live && !take) {
+                take[u] = live && d[u] <= (int)S.level;
+                if (live && !take[u]) {
                     keepm |= 1u << u;
                     ++nkeep;
                     local_min = min(local_min, (uint32_t)d[u]);
                 }
-                peel_take(take, v[u], S.round, S.level, rp, round_of, core, Fw, fcap, wr);
             }
+            peel_take_many<SCAN_PER_LANE>(take, v, S.round, S.level, rp, round_of, core, Fw, fcap, wr);
             uint32_t o = warp_reserve(nkeep, &wr->kept);
 #pragma unroll
             for (int u = 0; u < SCAN_PER_LANE; ++u)
@@ -285,18 +306,18 @@ __device__ __forceinline__ void peel_phase(const PeelState& S, uint32_t gwarp, u
             const uint32_t i = base + lane;
             uint2 it = make_uint2(0u, 0u);
             if (i < S.nf) it = __ldcg(&Fr[i]);
-            for (uint32_t t0 = 0; t0 < PEEL_CH; t0 += 4) {
+            for (uint32_t t0 = 0; t0 < PEEL_CH; t0 += PROC_STEP) {
                 if (__ballot_sync(0xffffffffu, it.y > t0) == 0) break;
-                uint32_t w[4];
-                int old[4];
+                uint32_t w[PROC_STEP];
+                int old[PROC_STEP];
+                bool take[PROC_STEP];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) w[u] = (t0 + u < it.y) ? __ldg(ci + it.x + t0 + u) : UNSET;
+                for (int u = 0; u < PROC_STEP; ++u) w[u] = (t0 + u < it.y) ? __ldg(ci + it.x + t0 + u) : UNSET;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) old[u] = (w[u] < n) ? atomicSub(&deg[w[u]], 1) : 0;
+                for (int u = 0; u < PROC_STEP; ++u) old[u] = (w[u] < n) ? atomicSub(&deg[w[u]], 1) : 0;
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    peel_take(w[u] < n && old[u] == (int)S.level + 1, w[u], S.round + 1, S.level, rp, round_of,
-                              core, Fw, fcap, wr);
+                for (int u = 0; u < PROC_STEP; ++u) take[u] = w[u] < n && old[u] == (int)S.level + 1;
+                peel_take_many<PROC_STEP>(take, w, S.round + 1, S.level, rp, round_of, core, Fw, fcap, wr);
             }
         }
     }
@@ -360,9 +381,10 @@ struct PeelCtl {
 };
 
 // A barrier wait gives up after this long (%globaltimer); the first one,
-// which also waits for every block of the launch to start, after START.
+// which also waits for every block of the launch to start (blocks of other
+// kernels may hold SMs until they finish), after START.
 static constexpr unsigned long long PEEL_BARRIER_NS = 2000000000ull;
-static constexpr unsigned long long PEEL_START_NS = 10000000000ull;
+static constexpr unsigned long long PEEL_START_NS = 60000000000ull;
 
 // Grid-wide barrier of the peel: arrivals only count up, and a block waits
 // until the count reaches its target (gridDim.x more per barrier), so no
@@ -764,13 +786,19 @@ kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, i
             uint32_t* corep = (uint32_t*)g->core.ptr;
             void* args[] = {(void*)&d_rp, (void*)&d_ci, (void*)&n, (void*)&deg, (void*)&round_of, (void*)&corep,
                             (void*)&F0, (void*)&F1, (void*)&fc, (void*)&R0, (void*)&R1, (void*)&pctl, (void*)&pout};
-            KC_TRY(cudaLaunchCooperativeKernel((const void*)k_peel_grid, dim3((unsigned)blocks), dim3(PEEL_THREADS),
-                                               args, 0, s));
-            note_launch();
             PeelOut hc;
-            KC_TRY(cudaMemcpyAsync(&hc, pout, sizeof(PeelOut), cudaMemcpyDeviceToHost, s));
-            KC_TRY(cudaMemcpyAsync(&maxdeg, words + 1, 4, cudaMemcpyDeviceToHost, s));
-            KC_TRY(cudaStreamSynchronize(s));
+            {
+                // one peel at a time in the process: two grid-wide launches must
+                // not each hold part of the SMs while waiting for the rest
+                static std::mutex peel_mu;
+                std::lock_guard<std::mutex> lock(peel_mu);
+                KC_TRY(cudaLaunchCooperativeKernel((const void*)k_peel_grid, dim3((unsigned)blocks),
+                                                   dim3(PEEL_THREADS), args, 0, s));
+                note_launch();
+                KC_TRY(cudaMemcpyAsync(&hc, pout, sizeof(PeelOut), cudaMemcpyDeviceToHost, s));
+                KC_TRY(cudaMemcpyAsync(&maxdeg, words + 1, 4, cudaMemcpyDeviceToHost, s));
+                KC_TRY(cudaStreamSynchronize(s));
+            }
             if (hc.flags & KC_FLAG_INTERNAL)
                 return fail(set_error(KC_E_INTERNAL, "k-core peel: inconsistent state after %u phases (level %u, "
                                                      "%u sub-rounds)", hc.phases, hc.max_level, hc.rounds));

@@ -1,24 +1,32 @@
 // Serving loop (include/kclique.h, kc_server_*): a pool of resident oriented
 // graphs and a worker thread that admits count queries as they arrive.
 //
-// Orientation-mode queries (pivot = 0) whose graphs fit the batched kernel
-// wait in one queue; whenever a slot (a stream with its own working memory)
-// is free, the worker packs up to max_batch of them into one persistent
-// launch (batch_launch), so queries that arrive while others run start on
-// the next free slot and their launches overlap on the device.  Each query's
-// result is published to host-mapped memory by the thread that completes its
-// last root, so it is served before the rest of its launch ends.  Pivot
-// queries, and orientation queries whose bitmaps need global memory, take a
-// slot each and run through the graph's own path (kc_count_async), at most
-// one per graph at a time (they share the graph's working memory).
-// Persistent launches hold their SMs until done, so every slot launches on a
-// fixed share of the SMs (SMs / slots) and a long launch cannot starve the
-// others.  A graph is admitted while the server's resident bytes stay within
-// its device-memory budget, and a graph-path query while the device reports
-// enough free memory for that path's buffers.  Waiting queries are admitted
-// cheapest first (by a size estimate), except that a query waiting longer
-// than a second goes before any cheaper one; the serial baseline keeps
-// arrival order.
+// With KC_SERVER_AUTO_TRAVERSAL and a time limit, adding a graph measures its
+// cost profile (profile_graph): which (k, traversal) shapes finish within the
+// limit on a slot's share of the SMs, and in how long.  A query takes the
+// traversal its profile says finishes, and KC_SERVER_REFUSE_EXPENSIVE
+// answers a shape that does not at once (KC_E_REFUSED).
+//
+// Orientation queries (pivot = 0) that the profile measured at most BATCH_MS
+// (or that have no profile) and whose graphs fit the batched kernel wait in
+// one queue; whenever a slot (a stream with its own working memory) is free,
+// the worker packs up to max_batch of them, their profiled times adding up to
+// at most half the time limit, into one persistent launch (batch_launch), so
+// queries that arrive while others run start on the next free slot and their
+// launches overlap on the device.  Each query's result is published to
+// host-mapped memory by the thread that completes its last root, so it is
+// served before the rest of its launch ends.  Pivot queries, longer
+// orientation queries, and orientation queries whose bitmaps need global
+// memory take a slot each and run through the graph's own path
+// (kc_count_async), at most one per graph at a time (they share the graph's
+// working memory).  Persistent launches hold their SMs until done, so every
+// slot launches on a fixed share of the SMs (SMs / slots) and a long launch
+// cannot starve the others.  A graph is admitted while the server's resident
+// bytes stay within its device-memory budget, and a graph-path query while
+// the device reports enough free memory for that path's buffers.  Waiting
+// queries are admitted cheapest first (by a size estimate), except that a
+// query waiting longer than a second goes before any cheaper one; the serial
+// baseline keeps arrival order.
 #include <stdio.h>
 #include <string.h>
 
@@ -135,6 +143,8 @@ static constexpr uint32_t SHAPE_KMAX = 128;
 static constexpr uint8_t SHAPE_UNKNOWN = 0, SHAPE_FITS = 1, SHAPE_EXPENSIVE = 2;
 // the cost profile measures the orientation traversal up to this k
 static constexpr uint32_t PROFILE_KMAX = 16;
+// profiled orientation queries longer than this skip the batched kernel
+static constexpr double BATCH_MS = 2.0;
 
 size_t shape_index(uint32_t k, int pivot) { return (size_t)std::min<uint32_t>(k, SHAPE_KMAX - 1) * 2 + (pivot ? 1 : 0); }
 
@@ -195,12 +205,21 @@ void take_cheapest(kc_server* S, std::deque<uint64_t>& q, uint32_t n, std::vecto
 void launch_batch(kc_server* S, BatchSlot& b) {
     take_cheapest(S, S->q_batch, (uint32_t)std::min<size_t>(S->q_batch.size(), S->max_batch), b.tickets);
     // item indices of a launch are 32-bit: queries beyond 2^31 roots wait for the next launch
+    // and one launch shares one deadline: its queries' profiled times add up
+    // to at most half the time limit (queries without a profile count 0)
     unsigned long long roots = 0;
+    double cost_ms = 0;
+    const double budget_ms = S->time_limit > 0 ? 0.5e3 * S->time_limit : 0;
     size_t keep = 0;
     while (keep < b.tickets.size()) {
-        const unsigned long long r = S->graphs[S->tickets[b.tickets[keep]].graph]->n;
+        const Ticket& T = S->tickets[b.tickets[keep]];
+        const unsigned long long r = S->graphs[T.graph]->n;
         if (keep > 0 && roots + r >= (1ull << 31)) break;
+        const size_t si = shape_index(T.k, 0);
+        const double c = S->shape_state[T.graph][si] == SHAPE_FITS ? S->shape_ms[T.graph][si] : 0.0;
+        if (keep > 0 && budget_ms > 0 && cost_ms + c > budget_ms) break;
         roots += r;
+        cost_ms += c;
         ++keep;
     }
     for (size_t i = b.tickets.size(); i-- > keep;) S->q_batch.push_front(b.tickets[i]);
@@ -620,7 +639,12 @@ kc_status kc_server_submit(kc_server* S, uint32_t graph_id, uint32_t k, int pivo
         return KC_OK;
     }
     pivot = T.pivot;
-    if (batchable(S->graphs[graph_id], k, pivot))
+    // a query the profile measured above BATCH_MS runs through its graph's
+    // own path (the single-graph kernels; one such query per graph at a time)
+    const size_t si = shape_index(k, 0);
+    const bool long_query = S->profiled[graph_id] && !pivot && S->shape_state[graph_id][si] == SHAPE_FITS &&
+                            S->shape_ms[graph_id][si] > BATCH_MS;
+    if (!long_query && batchable(S->graphs[graph_id], k, pivot))
         S->q_batch.push_back(id);
     else
         S->q_single.push_back(id);

@@ -465,6 +465,7 @@ def run_ours(a, g, plan, world, rank, local_rank):
         log(f"k = {a.deep_k} sub-record")
         kd = a.deep_k
         rr = torch.zeros(kclique.RESULT_BYTES, dtype=torch.uint8, device=dev)
+        G.set_time_limit(a.deep_limit)  # an unfinished count reports KC_E_TIMEOUT in "status"
         with torch.cuda.stream(stream):
             G.count_async(5, rr, scheme="ec", stream=stream)
         stream.synchronize()
@@ -481,7 +482,7 @@ def run_ours(a, g, plan, world, rank, local_rank):
         dms = d0.elapsed_time(d1)
         dops = 2.0 * rd.words
         deep = {"k": kd, "scheme": "ec", "status": kclique.status_name(rd.status), "count": str(rd.total),
-                "ms": dms, "cliques_per_s": rd.total / (dms / 1e3), "gpu_launches": kclique.launch_count() - launches_d0,
+                "ms": dms, "time_limit_s": a.deep_limit, "cliques_per_s": rd.total / (dms / 1e3), "gpu_launches": kclique.launch_count() - launches_d0,
                 "roofline": {"bound": "alu", "achieved": dops / (dms / 1e3) / 1e12, "peak": peak_alu,
                              "unit": "Tops/s", "frac": dops / (dms / 1e3) / 1e12 / peak_alu,
                              "kernel": "k_count_deep<EC> (one launch)", "ops": dops, "peak_note": rates["alu_note"]},
@@ -526,6 +527,94 @@ def run_ours(a, g, plan, world, rank, local_rank):
                                 "sample": f"k={k0}: every {cb['stride']}-th root with out-degree >= {k0 - 1} "
                                           f"({cb['roots']} roots, {cb['seconds']:.1f} s)"}
     return line
+
+
+# ----------------------------------------------------------------------------
+# the planted-community power-law graph: fixed-k totals and per-vertex counts
+# ----------------------------------------------------------------------------
+def chunglu_graph(seed=0):
+    """Chung-Lu, 4,000,000 vertices, exponent 2.1, mean degree 30, with 2,000
+    planted communities of 40-200 vertices at intra-edge probability 0.9."""
+    os.makedirs(CACHE, exist_ok=True)
+    path = os.path.join(CACHE, f"chunglu4m_c2000_s{seed}.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return synth.CSRGraph(int(z["n"]), z["row_ptr"], z["col_idx"], str(z["name"]))
+    g = synth.chung_lu_planted(4_000_000, 2.1, 30.0, ncomm=2000, size_min=40, size_max=200, p_in=0.9, seed=seed)
+    tmp = path + f".tmp{os.getpid()}.npz"
+    np.savez(tmp, n=g.n, row_ptr=g.row_ptr, col_idx=g.col_idx, name=g.name)
+    os.replace(tmp, path)
+    return g
+
+
+def run_chunglu(a, world, rank, local_rank):
+    """One degeneracy orientation, the k-clique total (orientation traversal)
+    and the per-vertex k-clique counts of the planted-community graph, each
+    under a time limit.  The per-vertex counts are checked by the identity
+    sum_v c_k(v) = k * c_k."""
+    import torch
+
+    from paper_2104_13209_gb300 import build, kclique
+
+    log("planted-community graph: generating")
+    g = chunglu_graph()
+    log(f"planted-community graph: {g.n} vertices, {g.num_edges} edges")
+    build.build()
+    kclique.load()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    rp_d = torch.from_numpy(g.row_ptr.view(np.int32)).to(dev)
+    ci_d = torch.from_numpy(g.col_idx.view(np.int32)).to(dev)
+    k = a.chunglu_k
+    rec = {"workload": g.name, "n": g.n, "edges": g.num_edges, "k": k, "time_limit_s": a.chunglu_limit}
+    launches0 = kclique.launch_count()
+    with ClockSampler(local_rank) as clk:
+        with torch.cuda.stream(stream):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            G = kclique.Graph(rp_d, ci_d, n=g.n, orient="degeneracy", validate=False, stream=stream)
+            e1.record(stream)
+        stream.synchronize()
+        rec["orient_ms"] = e0.elapsed_time(e1)
+        rec["d_max"] = G.info()["d_max"]
+        G.set_time_limit(a.chunglu_limit)
+        rr = torch.zeros(kclique.RESULT_BYTES, dtype=torch.uint8, device=dev)
+        with torch.cuda.stream(stream):
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            G.count_async(k, rr, scheme="ec", stream=stream)
+            c1.record(stream)
+        stream.synchronize()
+        r = kclique.parse_result(bytes(rr.cpu().numpy()))
+        ms = c0.elapsed_time(c1)
+        rates = device_rates(local_rank)
+        ops = 2.0 * r.words
+        rec["total"] = {"status": kclique.status_name(r.status), "count": str(r.total), "ms": ms,
+                        "cliques_per_s": r.total / (ms / 1e3), "flags": r.flags,
+                        "roofline": {"bound": "alu", "achieved": ops / (ms / 1e3) / 1e12, "peak": rates["alu_tops"],
+                                     "unit": "Tops/s", "frac": ops / (ms / 1e3) / 1e12 / rates["alu_tops"],
+                                     "kernel": "k_count_deep<EC> (one launch)", "ops": ops,
+                                     "peak_note": rates["alu_note"]}}
+        log(f"planted-community graph: k = {k} total {r.total} in {ms:.0f} ms ({kclique.status_name(r.status)})")
+        if a.chunglu_pv and r.status == kclique.KC_OK:
+            t0 = time.perf_counter()
+            try:
+                tot, pv, fl = G.count_per_vertex(k, pivot=False, stream=stream)
+                dt = time.perf_counter() - t0
+                s = int(pv.astype(object).sum())
+                rec["per_vertex"] = {"status": "KC_OK", "ms": 1e3 * dt, "total": str(tot), "flags": fl,
+                                     "sum_equals_k_times_total": s == k * tot,
+                                     "vertices_in_a_clique": int(np.count_nonzero(pv)),
+                                     "max": str(int(pv.max())), "timed": "host clock around the synchronous "
+                                     "call, per-vertex array copied to the host inside"}
+            except kclique.KCError as e:
+                rec["per_vertex"] = {"status": kclique.status_name(e.status), "ms": 1e3 * (time.perf_counter() - t0)}
+            log(f"planted-community graph: per-vertex {rec['per_vertex']['status']}")
+        G.close()
+    rec["clocks"] = clk.summary()
+    rec["gpu_launches"] = kclique.launch_count() - launches0
+    return rec
 
 
 # ----------------------------------------------------------------------------
@@ -729,15 +818,20 @@ def main():
     ap.add_argument("--scale", type=int, default=20)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "batch", "serve"])
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "batch", "serve", "chunglu"])
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=0.5)
     ap.add_argument("--time-limit", type=float, default=0.25)
     ap.add_argument("--serve-modes", default="batched,plain")
     ap.add_argument("--sub", default="batch,serve",
-                    help="sub-records of the default line: batch, serve (one GPU only; empty: none)")
+                    help="sub-records of the default line: batch, serve, chunglu (one GPU only; empty: none)")
     ap.add_argument("--deep-k", type=int, default=7,
                     help="also time one count of this size on the same graph (0: skip)")
+    ap.add_argument("--deep-limit", type=float, default=120.0,
+                    help="time limit (s) of that count")
+    ap.add_argument("--chunglu-k", type=int, default=8)
+    ap.add_argument("--chunglu-limit", type=float, default=180.0, help="time limit (s) of each planted-community count")
+    ap.add_argument("--chunglu-pv", type=int, default=1, help="also the per-vertex counts (0: skip)")
     a = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -753,6 +847,9 @@ def main():
         return
     if a.workload == "serve" and a.impl == "ours":
         print(json.dumps(run_serve(a, world, rank, local_rank)), flush=True)
+        return
+    if a.workload == "chunglu" and a.impl == "ours":
+        print(json.dumps(run_chunglu(a, world, rank, local_rank)), flush=True)
         return
     g = workload_graph(a.scale)
     plan = parse_plan(a.plan)
@@ -770,6 +867,8 @@ def main():
         if "serve" in subs:
             sv = run_serve(a, world, rank, local_rank)
             line["served"] = {k: sv[k] for k in ("value", "unit", "config", "latency_ms", "served", "mismatches")}
+        if "chunglu" in subs:
+            line["planted_community"] = run_chunglu(a, world, rank, local_rank)
         if rank == 0:
             print(json.dumps(line), flush=True)
     if world > 1:

@@ -289,9 +289,11 @@ kc_status kc_batch_set_time_limit(kc_batch* b, double seconds);
  * 1).  Results go to results_dev[i] (device memory, nq entries): total and
  * total_hi (exact below 2^128), KC_FLAG_* flags, status KC_OK or
  * KC_E_TIMEOUT.  tune (nullable): configuration per bucket; buckets it does
- * not list take the paper's guideline (Section 4.5).  Stream-ordered; the
- * call may wait for its own previous call's descriptor copy and may
- * allocate, so use kc_batch_capture for CUDA-graph replay. */
+ * not list take the paper's guideline (Section 4.5).  Queries that share a
+ * launch configuration form one launch, whose roots must number fewer than
+ * 2^31 (KC_E_UNSUPPORTED otherwise).  Stream-ordered; the call may wait for
+ * its own previous call's descriptor copy and may allocate, so use
+ * kc_batch_capture for CUDA-graph replay. */
 kc_status kc_batch_count(kc_batch* b, const uint32_t* graph_ids, const uint32_t* ks, uint32_t nq,
                          kc_result* results_dev, const kc_tune* tune, void* stream);
 

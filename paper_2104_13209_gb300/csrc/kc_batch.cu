@@ -213,11 +213,13 @@ static kc_status make_plan(const kc_batch* b, const uint32_t* graph_ids, const u
         }
     }
     for (Group& G : P.groups) {
-        // item indices of a launch are 32-bit: its queries' roots must number fewer than 2^32
+        // item indices of a launch are 32-bit, and once the work runs out every
+        // warp and block still advances the claim cursors by one chunk: below
+        // 2^31 roots the cursors cannot wrap (the server's launches use the same bound)
         unsigned long long items = 0;
         for (uint32_t i = G.first; i < G.first + G.count; ++i) items += P.q[i].n_roots;
-        if (items >= (1ull << 32))
-            return set_error(KC_E_UNSUPPORTED, "one launch would hold %llu roots (at most 2^32 - 1)", items);
+        if (items >= (1ull << 31))
+            return set_error(KC_E_UNSUPPORTED, "one launch would hold %llu roots (at most 2^31 - 1)", items);
         if (G.k_max >= 3 && !batch_smem_bytes(G.d_cap, G.k_max, G.cfg))
             return set_error(KC_E_UNSUPPORTED, "a graph's out-degree %u is too large for a batched launch", G.d_cap);
         G.ws_off = off_ws;

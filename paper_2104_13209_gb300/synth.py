@@ -99,14 +99,16 @@ def edges_to_csr(n: int, u: np.ndarray, v: np.ndarray, name: str = "") -> CSRGra
     keep = u != v
     lo = np.minimum(u[keep], v[keep]).astype(np.uint64)
     hi = np.maximum(u[keep], v[keep]).astype(np.uint64)
-    key = np.unique(lo * np.uint64(n) + hi)
+    key = lo * np.uint64(n) + hi
+    key.sort()  # sorted distinct keys (the same values as np.unique, much faster at 10^8 keys)
+    if key.size:
+        key = key[np.concatenate(([True], key[1:] != key[:-1]))]
     lo = (key // np.uint64(n)).astype(np.int64)
     hi = (key % np.uint64(n)).astype(np.int64)
-    src = np.concatenate([lo, hi])
-    dst = np.concatenate([hi, lo])
-    order = np.argsort(src.astype(np.uint64) * np.uint64(n) + dst.astype(np.uint64), kind="stable")
-    src = src[order]
-    dst = dst[order]
+    both = np.concatenate([key, hi.astype(np.uint64) * np.uint64(n) + lo.astype(np.uint64)])
+    both.sort()  # every (src, dst) once, ordered by source then destination
+    src = (both // np.uint64(n)).astype(np.int64)
+    dst = (both % np.uint64(n)).astype(np.int64)
     if dst.size >= (1 << 32):
         raise ValueError("nnz does not fit in u32")
     counts = np.bincount(src, minlength=n)

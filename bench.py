@@ -478,7 +478,7 @@ def run_ours(a, g, plan, world, rank, local_rank):
                 G.count_async(kd, rr, scheme="ec", stream=stream)
                 d1.record(stream)
             stream.synchronize()
-        rd = kclique.parse_result(bytes(rr.cpu().numpy()))
+        rd = kclique.parse_results(bytes(rr.cpu().numpy()), 1)[0]  # a timed-out count reports its status
         dms = d0.elapsed_time(d1)
         dops = 2.0 * rd.words
         deep = {"k": kd, "scheme": "ec", "status": kclique.status_name(rd.status), "count": str(rd.total),
@@ -548,10 +548,10 @@ def chunglu_graph(seed=0):
 
 
 def run_chunglu(a, world, rank, local_rank):
-    """One degeneracy orientation, the k-clique total (orientation traversal)
-    and the per-vertex k-clique counts of the planted-community graph, each
-    under a time limit.  The per-vertex counts are checked by the identity
-    sum_v c_k(v) = k * c_k."""
+    """One degeneracy orientation, then the k-clique totals (orientation
+    traversal) for each k of --chunglu-k and the per-vertex counts for each
+    k of --chunglu-pv-k, every count under --chunglu-limit seconds.  The
+    per-vertex counts are checked by the identity sum_v c_k(v) = k * c_k."""
     import torch
 
     from paper_2104_13209_gb300 import build, kclique
@@ -566,8 +566,11 @@ def run_chunglu(a, world, rank, local_rank):
     stream = torch.cuda.Stream(device=dev)
     rp_d = torch.from_numpy(g.row_ptr.view(np.int32)).to(dev)
     ci_d = torch.from_numpy(g.col_idx.view(np.int32)).to(dev)
-    k = a.chunglu_k
-    rec = {"workload": g.name, "n": g.n, "edges": g.num_edges, "k": k, "time_limit_s": a.chunglu_limit}
+    ks = [int(x) for x in str(a.chunglu_k).split(",") if x]
+    pks = [int(x) for x in str(a.chunglu_pv_k).split(",") if x]
+    rec = {"workload": g.name, "n": g.n, "edges": g.num_edges, "time_limit_s": a.chunglu_limit, "totals": {},
+           "per_vertex": {}}
+    rates = device_rates(local_rank)
     launches0 = kclique.launch_count()
     with ClockSampler(local_rank) as clk:
         with torch.cuda.stream(stream):
@@ -580,37 +583,40 @@ def run_chunglu(a, world, rank, local_rank):
         rec["d_max"] = G.info()["d_max"]
         G.set_time_limit(a.chunglu_limit)
         rr = torch.zeros(kclique.RESULT_BYTES, dtype=torch.uint8, device=dev)
-        with torch.cuda.stream(stream):
-            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            c0.record(stream)
-            G.count_async(k, rr, scheme="ec", stream=stream)
-            c1.record(stream)
-        stream.synchronize()
-        r = kclique.parse_result(bytes(rr.cpu().numpy()))
-        ms = c0.elapsed_time(c1)
-        rates = device_rates(local_rank)
-        ops = 2.0 * r.words
-        rec["total"] = {"status": kclique.status_name(r.status), "count": str(r.total), "ms": ms,
-                        "cliques_per_s": r.total / (ms / 1e3), "flags": r.flags,
-                        "roofline": {"bound": "alu", "achieved": ops / (ms / 1e3) / 1e12, "peak": rates["alu_tops"],
-                                     "unit": "Tops/s", "frac": ops / (ms / 1e3) / 1e12 / rates["alu_tops"],
-                                     "kernel": "k_count_deep<EC> (one launch)", "ops": ops,
-                                     "peak_note": rates["alu_note"]}}
-        log(f"planted-community graph: k = {k} total {r.total} in {ms:.0f} ms ({kclique.status_name(r.status)})")
-        if a.chunglu_pv and r.status == kclique.KC_OK:
+        for k in ks:
+            with torch.cuda.stream(stream):
+                c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
+                G.count_async(k, rr, scheme="ec", stream=stream)
+                c1.record(stream)
+            stream.synchronize()
+            r = kclique.parse_results(bytes(rr.cpu().numpy()), 1)[0]
+            ms = c0.elapsed_time(c1)
+            ops = 2.0 * r.words
+            rec["totals"][str(k)] = {
+                "status": kclique.status_name(r.status), "count": str(r.total) if r.status == kclique.KC_OK else None,
+                "ms": ms, "cliques_per_s": r.total / (ms / 1e3) if r.status == kclique.KC_OK else None,
+                "flags": r.flags,
+                "roofline": {"bound": "alu", "achieved": ops / (ms / 1e3) / 1e12, "peak": rates["alu_tops"],
+                             "unit": "Tops/s", "frac": ops / (ms / 1e3) / 1e12 / rates["alu_tops"],
+                             "kernel": "k_count_deep<EC> (one launch)" if k >= 5 else "k_count_orient<EC>",
+                             "ops": ops, "peak_note": rates["alu_note"]}}
+            log(f"planted-community graph: k = {k} total {r.total} in {ms:.0f} ms ({kclique.status_name(r.status)})")
+        for k in pks:
             t0 = time.perf_counter()
             try:
                 tot, pv, fl = G.count_per_vertex(k, pivot=False, stream=stream)
                 dt = time.perf_counter() - t0
                 s = int(pv.astype(object).sum())
-                rec["per_vertex"] = {"status": "KC_OK", "ms": 1e3 * dt, "total": str(tot), "flags": fl,
-                                     "sum_equals_k_times_total": s == k * tot,
-                                     "vertices_in_a_clique": int(np.count_nonzero(pv)),
-                                     "max": str(int(pv.max())), "timed": "host clock around the synchronous "
-                                     "call, per-vertex array copied to the host inside"}
+                rec["per_vertex"][str(k)] = {
+                    "status": "KC_OK", "ms": 1e3 * dt, "total": str(tot), "flags": fl,
+                    "sum_equals_k_times_total": s == k * tot, "vertices_in_a_clique": int(np.count_nonzero(pv)),
+                    "max": str(int(pv.max())),
+                    "timed": "host clock around the synchronous call (per-vertex array copied to the host inside)"}
             except kclique.KCError as e:
-                rec["per_vertex"] = {"status": kclique.status_name(e.status), "ms": 1e3 * (time.perf_counter() - t0)}
-            log(f"planted-community graph: per-vertex {rec['per_vertex']['status']}")
+                rec["per_vertex"][str(k)] = {"status": kclique.status_name(e.status),
+                                             "ms": 1e3 * (time.perf_counter() - t0)}
+            log(f"planted-community graph: per-vertex k = {k}: {rec['per_vertex'][str(k)]['status']}")
         G.close()
     rec["clocks"] = clk.summary()
     rec["gpu_launches"] = kclique.launch_count() - launches0
@@ -829,9 +835,9 @@ def main():
                     help="also time one count of this size on the same graph (0: skip)")
     ap.add_argument("--deep-limit", type=float, default=120.0,
                     help="time limit (s) of that count")
-    ap.add_argument("--chunglu-k", type=int, default=8)
+    ap.add_argument("--chunglu-k", default="7,8", help="sizes of the planted-community totals")
     ap.add_argument("--chunglu-limit", type=float, default=180.0, help="time limit (s) of each planted-community count")
-    ap.add_argument("--chunglu-pv", type=int, default=1, help="also the per-vertex counts (0: skip)")
+    ap.add_argument("--chunglu-pv-k", default="7", help="sizes of the planted-community per-vertex counts")
     a = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

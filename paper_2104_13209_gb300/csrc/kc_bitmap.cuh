@@ -110,25 +110,93 @@ __host__ __device__ __forceinline__ uint32_t hash_bits_for(uint32_t d) {
     return b;
 }
 
-// 32-bit words of the table for candidate sets up to d (16-bit slots)
-__host__ __device__ __forceinline__ uint32_t hash_table_words(uint32_t d) { return (1u << hash_bits_for(d)) / 2; }
+// Candidate filter beside the table: one bit per slot of a larger hash
+// range, set for every candidate (bit hash_slot(y, fbits)).  A clear bit
+// proves that y is not a candidate; a set bit (a candidate, or a false
+// positive at a rate of at most 1/32) sends y to the table.  At least 32
+// slots per candidate, at least 1,024.
+__host__ __device__ __forceinline__ uint32_t filter_bits_for(uint32_t d) {
+    uint32_t b = 10;
+    while ((1u << b) < 32 * d) ++b;
+    return b;
+}
 
-// Same rows as build_bitmap, with the table above instead of binary search.
-// tab: hash_table_words(d) words, 2^tbits 16-bit slots (tbits from
-// hash_bits_for(d)); d < 65535.
+__host__ __device__ __forceinline__ uint32_t filter_words(uint32_t d) { return (1u << filter_bits_for(d)) >> 5; }
+
+// 32-bit words of the table and its filter for candidate sets up to d
+// (both grow with d, so a smaller set fits the space of a larger one)
+__host__ __device__ __forceinline__ uint32_t hash_table_words(uint32_t d) {
+    return (1u << hash_bits_for(d)) / 2 + filter_words(d);
+}
+
+// The entries y of the sorted DAG row col[b, e) whose filter bit is set
+// (bit hash_slot(y, fbits) of filt), handed to f(y) by the 32 lanes of a
+// warp.  Each lane loads two 16-byte quads per round (256 entries per warp
+// round, all loads in flight) and tests its 8 entries without branching;
+// only the entries that pass are handed to f, one after another.  Filtering
+// first keeps the lanes of a warp together: the data-dependent work (the
+// exact lookup of about one entry in eight) runs as one loop per round
+// instead of once per entry.  The scan stops after the round whose final
+// entry exceeds last.  The row array must be 16-byte aligned and readable up
+// to the quad holding entry e - 1; filt is read at words below 2^fbits / 32.
+template <class F>
+__device__ __forceinline__ void scan_row_filtered(const uint32_t* __restrict__ col, uint32_t b, uint32_t e,
+                                                  uint32_t last, int lane, const uint32_t* filt, uint32_t fbits,
+                                                  F&& f) {
+    const uint4* col4 = reinterpret_cast<const uint4*>(col);
+    const uint32_t qend = (e + 3) >> 2;
+    const uint32_t len = e - b;
+    for (uint32_t q0 = b >> 2; q0 < qend; q0 += 64) {
+        const uint32_t qa = q0 + lane, qb = qa + 32;
+        uint4 va = make_uint4(NONE, NONE, NONE, NONE), vb = va;
+        if (qa < qend) va = __ldg(col4 + qa);
+        if (qb < qend) vb = __ldg(col4 + qb);
+        const uint32_t y[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+        // offsets of the quads' first entries within the row; entries before
+        // b wrap to large values, so one unsigned compare keeps [b, e)
+        const uint32_t ta = (qa << 2) - b, tb = (qb << 2) - b;
+        uint32_t pend = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint32_t t = (c < 4 ? ta : tb) + (uint32_t)(c & 3);
+            const uint32_t hf = hash_slot(y[c], fbits);
+            const uint32_t bit = (filt[hf >> 5] >> (hf & 31)) & 1u;
+            pend |= (t < len ? bit : 0u) << c;
+        }
+        while (pend) {
+            const int c = __ffs(pend) - 1;
+            pend &= pend - 1;
+            uint32_t yc = y[0];
+#pragma unroll
+            for (int x = 1; x < 8; ++x) yc = (c == x) ? y[x] : yc;
+            f(yc);
+        }
+        const uint32_t tail = ((qb << 2) + 3 < e) ? vb.w : NONE;
+        if (__shfl_sync(0xffffffffu, tail, 31) >= last) break;  // the rest of the row lies beyond last
+    }
+}
+
+// Same rows as build_bitmap, with the table and filter above instead of
+// binary search.  tab: hash_table_words(d) words: 2^tbits 16-bit slots
+// (tbits from hash_bits_for(d)), then the filter (filter_bits_for(d) bits);
+// d < 65535.
 template <int NT>
 __device__ void build_bitmap_hashed(const uint32_t* __restrict__ rp, const uint32_t* __restrict__ col,
                                     const uint32_t* cand, uint32_t d, uint32_t W, uint32_t* bm, uint32_t* tabw,
                                     uint32_t tbits) {
     const uint32_t T = 1u << tbits, mask = T - 1;
-    uint32_t* tw = tabw;
+    const uint32_t fbits = filter_bits_for(d);
     uint16_t* tab = reinterpret_cast<uint16_t*>(tabw);
+    uint32_t* filt = tabw + T / 2;
     for (uint32_t x = threadIdx.x; x < d * W; x += NT) bm[x] = 0;
-    for (uint32_t x = threadIdx.x; x < T / 2; x += NT) tw[x] = 0;
+    for (uint32_t x = threadIdx.x; x < T / 2 + filter_words(d); x += NT) tabw[x] = 0;
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < d; i += NT) {
-        uint32_t h = hash_slot(cand[i], tbits);
+        const uint32_t y = cand[i];
+        uint32_t h = hash_slot(y, tbits);
         while (atomicCAS(&tab[h], (unsigned short)0, (unsigned short)(i + 1)) != 0) h = (h + 1) & mask;
+        const uint32_t hf = hash_slot(y, fbits);
+        atomicOr(&filt[hf >> 5], 1u << (hf & 31));
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -147,7 +215,7 @@ __device__ void build_bitmap_hashed(const uint32_t* __restrict__ rp, const uint3
             ne = __ldg(rp + x2 + 1);
         }
         uint32_t* row = bm + (size_t)i * W;
-        scan_row(col, b, e, last, lane, [&](uint32_t y) {
+        scan_row_filtered(col, b, e, last, lane, filt, fbits, [&](uint32_t y) {
             uint32_t h = hash_slot(y, tbits);
             for (;;) {
                 const uint32_t p = tab[h];

@@ -126,6 +126,7 @@ static __device__ uint32_t next_big_slot(const CountParams& P, WorkCtl* wc, int&
 // ---------------------------------------------------------------------------
 struct WarpShared {
     uint32_t cand[32];
+    uint32_t filt[32];     // candidate filter (1,024 bits: one word per bank, so lookups never conflict)
     uint32_t row[32];
     uint32_t pre[32];      // exclusive prefix of the rows' popcounts (level-3 task numbering)
     uint32_t next;         // next unclaimed level-3 task
@@ -187,20 +188,31 @@ static __device__ void warp_root(const CountParams& P, const uint32_t* __restric
     const uint32_t rem0 = k - 2;  // below the root edge u -> cand[lane]
     const uint32_t b = rp[u];
     const uint32_t d = rp[u + 1] - b;
-    if (lane < (int)d) ws.cand[lane] = col[b + lane];
+    constexpr uint32_t FBITS = 10;  // 1,024 filter bits for at most 32 candidates
+    uint32_t cu = 0;
+    if (lane < (int)d) {
+        cu = col[b + lane];
+        ws.cand[lane] = cu;
+    }
+    ws.filt[lane] = 0;
+    __syncwarp();
+    if (lane < (int)d) {
+        const uint32_t hf = hash_slot(cu, FBITS);
+        atomicOr(&ws.filt[hf >> 5], 1u << (hf & 31));
+    }
     __syncwarp();
     // rows, one per candidate, built cooperatively (lanes over N+(cand[r]));
     // lane r holds the bounds of row r, loaded together
     const uint32_t last = ws.cand[d - 1];
     uint32_t rb = 0, re = 0;
     if (lane < (int)d) {
-        rb = __ldg(rp + ws.cand[lane]);
-        re = __ldg(rp + ws.cand[lane] + 1);
+        rb = __ldg(rp + cu);
+        re = __ldg(rp + cu + 1);
     }
     for (uint32_t r = 0; r < d; ++r) {
         const uint32_t xb = __shfl_sync(0xffffffffu, rb, r), xe = __shfl_sync(0xffffffffu, re, r);
         uint32_t bits = 0;
-        scan_row(col, xb, xe, last, lane, [&](uint32_t y) {
+        scan_row_filtered(col, xb, xe, last, lane, ws.filt, FBITS, [&](uint32_t y) {
             const uint32_t pos = find_sorted(ws.cand, r + 1, d, y);
             if (pos != NONE) bits |= 1u << pos;
         });

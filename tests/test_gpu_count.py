@@ -120,6 +120,26 @@ def test_rmat20_full_size_k4():
         G.close()
 
 
+def test_rmat16_deep_k_golden():
+    """R-MAT scale 16 (edge factor 16; 219 candidates at most under degeneracy
+    order, so the deep traversal's wide levels and its re-encoded nodes both
+    run) at the deep sizes the R-MAT-20 configuration asks for, k = 5, 6 and
+    7: both schemes, both orientations, against the oracle's totals stored by
+    tests/golden/make_golden.py."""
+    with open(os.path.join(GOLDEN, "counts.json")) as f:
+        rec = json.load(f)["rmat16_ef16_s0"]
+    g = synth.rmat(16, 16, seed=0)
+    assert g.num_edges == rec["num_edges"]
+    for orient in ("degeneracy", "degree"):
+        G = graph(g, orient)
+        if orient == "degeneracy":
+            assert G.info()["d_max"] == rec["degeneracy_dmax"]
+        for k in sorted(int(x) for x in rec["counts"]):
+            for scheme in ("vc", "ec"):
+                assert G.count(k, scheme=scheme).total == rec["counts"][str(k)], (orient, k, scheme)
+        G.close()
+
+
 def test_time_limit_returns_timeout_and_keeps_the_handle():
     # billions of 9-cliques: cannot finish in 50 ms; the wait ends with a
     # status, the context and the handle stay usable

@@ -475,18 +475,27 @@ def run_ours(a, g, plan, world, rank, local_rank):
                 d0 = torch.cuda.Event(enable_timing=True)
                 d1 = torch.cuda.Event(enable_timing=True)
                 d0.record(stream)
-                G.count_async(kd, rr, scheme="ec", stream=stream)
+                if a.deep_pivot:
+                    G.count_async(kd, rr, pivot=True, stream=stream)
+                else:
+                    G.count_async(kd, rr, scheme="ec", stream=stream)
                 d1.record(stream)
             stream.synchronize()
         rd = kclique.parse_results(bytes(rr.cpu().numpy()), 1)[0]  # a timed-out count reports its status
         dms = d0.elapsed_time(d1)
-        dops = 2.0 * rd.words
-        deep = {"k": kd, "scheme": "ec", "status": kclique.status_name(rd.status), "count": str(rd.total),
-                "ms": dms, "time_limit_s": a.deep_limit, "cliques_per_s": rd.total / (dms / 1e3), "gpu_launches": kclique.launch_count() - launches_d0,
-                "roofline": {"bound": "alu", "achieved": dops / (dms / 1e3) / 1e12, "peak": peak_alu,
-                             "unit": "Tops/s", "frac": dops / (dms / 1e3) / 1e12 / peak_alu,
-                             "kernel": "k_count_deep<EC> (one launch)", "ops": dops, "peak_note": rates["alu_note"]},
-                "clocks": clk_d.summary()}
+        ok = rd.status == kclique.KC_OK
+        deep = {"k": kd, "traversal": "pivot (fixed k)" if a.deep_pivot else "orientation, edge-centric",
+                "status": kclique.status_name(rd.status), "count": str(rd.total) if ok else None,
+                "ms": dms, "time_limit_s": a.deep_limit, "cliques_per_s": rd.total / (dms / 1e3) if ok else None,
+                "gpu_launches": kclique.launch_count() - launches_d0, "clocks": clk_d.summary()}
+        if a.deep_pivot:
+            deep["tree_nodes"] = rd.words
+            deep["tree_nodes_per_s"] = rd.words / (dms / 1e3)
+        else:
+            dops = 2.0 * rd.words
+            deep["roofline"] = {"bound": "alu", "achieved": dops / (dms / 1e3) / 1e12, "peak": peak_alu,
+                                "unit": "Tops/s", "frac": dops / (dms / 1e3) / 1e12 / peak_alu,
+                                "kernel": "k_count_deep<EC> (one launch)", "ops": dops, "peak_note": rates["alu_note"]}
     G.close()
 
     clocks = clk.summary()
@@ -835,6 +844,7 @@ def main():
                     help="also time one count of this size on the same graph (0: skip)")
     ap.add_argument("--deep-limit", type=float, default=120.0,
                     help="time limit (s) of that count")
+    ap.add_argument("--deep-pivot", action="store_true", help="count that size by the pivoting traversal")
     ap.add_argument("--chunglu-k", default="7,8", help="sizes of the planted-community totals")
     ap.add_argument("--chunglu-limit", type=float, default=180.0, help="time limit (s) of each planted-community count")
     ap.add_argument("--chunglu-pv-k", default="7", help="sizes of the planted-community per-vertex counts")

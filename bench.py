@@ -633,6 +633,72 @@ def run_chunglu(a, world, rank, local_rank):
 
 
 # ----------------------------------------------------------------------------
+# the paper's ablation (Section 4.3, Figs. 6 and 7) on the R-MAT workload
+# ----------------------------------------------------------------------------
+def run_ablation(a, g, world, rank, local_rank):
+    """Binary-encoded bitmaps against sorted lists (schemes vc/ec against
+    vc-list/ec-list), every sub-warp width of the bitmap traversal, and the
+    per-SM split of each count's work units (load balance, max / mean over
+    the SMs), each count timed alone with CUDA events after an L2 flush."""
+    import torch
+
+    from paper_2104_13209_gb300 import build, kclique
+
+    build.build()
+    kclique.load()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    rp_d = torch.from_numpy(g.row_ptr.view(np.int32)).to(dev)
+    ci_d = torch.from_numpy(g.col_idx.view(np.int32)).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    rr = torch.zeros(kclique.RESULT_BYTES, dtype=torch.uint8, device=dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    with torch.cuda.stream(stream):
+        G = kclique.Graph(rp_d, ci_d, n=g.n, orient="degeneracy", validate=False, stream=stream)
+    stream.synchronize()
+    G.set_time_limit(a.deep_limit)
+
+    def one(k, scheme, subwarp=0):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            G.count_async(k, rr, scheme=scheme, subwarp=subwarp, stream=stream)
+            e1.record(stream)
+        stream.synchronize()
+        r = kclique.parse_results(bytes(rr.cpu().numpy()), 1)[0]
+        w = G.last_sm_work()[:sms].astype(np.float64)
+        mean = float(w.mean()) if w.size else 0.0
+        return {"k": k, "scheme": scheme, "subwarp": subwarp, "status": kclique.status_name(r.status),
+                "count": str(r.total), "ms": e0.elapsed_time(e1), "work_units": r.words,
+                "sm_work_max_over_mean": float(w.max()) / mean if mean > 0 else None,
+                "sm_work_cv": float(w.std()) / mean if mean > 0 else None}
+
+    log("ablation: warm-up")
+    for scheme in ("vc", "ec", "vc-list", "ec-list"):
+        one(3, scheme)
+    runs = []
+    for k in (3, 4):
+        for scheme in ("vc", "ec", "vc-list", "ec-list"):
+            runs.append(one(k, scheme))
+            log(f"ablation: k = {k} {scheme}: {runs[-1]['ms']:.2f} ms")
+    sweep = []
+    for scheme in ("vc", "ec"):
+        for sw in (1, 2, 4, 8, 16, 32):
+            sweep.append(one(4, scheme, sw))
+    G.close()
+    by = {(r["k"], r["scheme"]): r for r in runs}
+    ratios = {f"k{k}_{s}": by[(k, s + "-list")]["ms"] / by[(k, s)]["ms"] for k in (3, 4) for s in ("vc", "ec")}
+    best = {s: min(x["ms"] for x in sweep if x["scheme"] == s) for s in ("vc", "ec")}
+    worst = {s: max(x["ms"] for x in sweep if x["scheme"] == s) for s in ("vc", "ec")}
+    return {"metric": METRIC, "workload": g.name, "orientation": "degeneracy", "runs": runs,
+            "list_over_bitmap_time": ratios, "subwarp_sweep_k4": sweep,
+            "subwarp_best_over_worst": {s: worst[s] / best[s] for s in ("vc", "ec")},
+            "l2": f"flushed before each count ({L2_FLUSH_BYTES >> 20} MiB write)", "sms": sms}
+
+
+# ----------------------------------------------------------------------------
 # batched and serving workloads (many small graphs; a stream of queries)
 # ----------------------------------------------------------------------------
 def run_batch(a, world, rank, local_rank):
@@ -833,7 +899,7 @@ def main():
     ap.add_argument("--scale", type=int, default=20)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "batch", "serve", "chunglu"])
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "batch", "serve", "chunglu", "ablation"])
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=0.5)
     ap.add_argument("--time-limit", type=float, default=0.25)
@@ -868,6 +934,9 @@ def main():
         print(json.dumps(run_chunglu(a, world, rank, local_rank)), flush=True)
         return
     g = workload_graph(a.scale)
+    if a.workload == "ablation" and a.impl == "ours":
+        print(json.dumps(run_ablation(a, g, world, rank, local_rank)), flush=True)
+        return
     plan = parse_plan(a.plan)
     if a.impl == "reference":
         run_reference(a, g, plan, world, rank)

@@ -61,6 +61,15 @@ typedef int kc_status;
 #define KC_SCHEME_AUTO 0        /* vertex-centric for k < 6, edge-centric otherwise (Section 4.5) */
 #define KC_SCHEME_VC 1          /* one root vertex per work item */
 #define KC_SCHEME_EC 2          /* one root edge per work item */
+/* The same two splits without the binary encoding (the paper's comparison
+ * point, Sections 3.4 and 4.3): candidate sets are sorted vertex lists and
+ * each intersection searches the members of one list in a DAG row (binary
+ * search).  Orientation traversal only, totals only (per-vertex counts give
+ * KC_E_UNSUPPORTED), 3 <= k <= 16 (KC_E_UNSUPPORTED beyond); one warp per
+ * root vertex (VC_LIST) or per DAG edge (EC_LIST).  Work units: membership
+ * tests. */
+#define KC_SCHEME_VC_LIST 3
+#define KC_SCHEME_EC_LIST 4
 
 /* Result flag bits. */
 #define KC_FLAG_TOTAL_OVERFLOW 1u       /* the total exceeded 2^64 - 1 */
@@ -134,6 +143,18 @@ kc_status kc_graph_set_time_limit(kc_graph* g, double seconds);
  * search-tree nodes analysed (a pivot search each). */
 kc_status kc_graph_last_work(const kc_graph* g, uint64_t* units);
 
+/* The same work units of the last orientation-mode count on this graph
+ * (kc_count and kc_count_async with pivot = 0), split by the SM that did
+ * them: the load balance across SMs of Section 4.4 (Fig. 7).
+ *   per_sm (host, cap entries, nullable when cap = 0): per_sm[i] = units done
+ *     on SM i (the %smid of the warps that did them); entries beyond the
+ *     library's 1,024 slots are 0.
+ *   slots_out (host): the number of slots that hold the count: the device's
+ *     SM count, or more if a higher SM id reported work.
+ * Reads the counters with a synchronous copy: call it after the count has
+ * finished.  Before any count, or after k <= 2, every entry is 0. */
+kc_status kc_graph_last_sm_work(const kc_graph* g, uint64_t* per_sm, uint32_t cap, uint32_t* slots_out);
+
 /* Copy the oriented graph to host memory (for inspection and tests).
  *   dag_row_ptr[n+1], dag_col[num_edges]: the DAG in the library's vertex
  *     numbering, where vertex r is the r-th vertex of the orientation order,
@@ -150,15 +171,16 @@ kc_status kc_graph_export(const kc_graph* g, uint32_t* dag_row_ptr, uint32_t* da
  *   pivot: 0 = graph-orientation traversal (Fig. 2); 1 = pivoting traversal
  *     restricted to size k (Fig. 3, stopping when more than k vertices are
  *     held).
- *   scheme: KC_SCHEME_AUTO / VC / EC.
+ *   scheme: KC_SCHEME_AUTO / VC / EC / VC_LIST / EC_LIST.
  *   subwarp: threads per group for the big-subgraph path, 0 = automatic,
  *     else 1, 2, 4, 8, 16 or 32 (Section 3.5).
  *   total_out (host): the count modulo 2^64.
  *   per_vertex_out (nullable, n entries, host or device memory): c_k(v), the
- *     number of k-cliques containing input vertex v, modulo 2^64.  These
- *     always come from the pivoting traversal restricted to size k, and so
- *     does the total of such a call, whatever `pivot` says (the counts are
- *     the same).
+ *     number of k-cliques containing input vertex v, modulo 2^64.  With
+ *     pivot = 0 they come from the graph-orientation traversal for
+ *     3 <= k <= 36 when its shared-memory geometry fits the graph; otherwise
+ *     (and with pivot = 1) from the pivoting traversal restricted to size k,
+ *     which then gives the total too (the counts are the same).
  *   flags_out (nullable, host): KC_FLAG_* bits.
  * Returns KC_E_OVERFLOW (with every output written) when the total or a
  * per-vertex count exceeded 2^64 - 1. */

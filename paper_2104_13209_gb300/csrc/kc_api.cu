@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <new>
 #include <string>
@@ -119,7 +120,7 @@ static bool is_device_pointer(const void* p) {
 
 uint64_t kc_graph::device_bytes() const {
     const kc::DevBuf* bufs[] = {&row_ptr, &col, &new_of_old, &old_of_new, &core, &roots, &ctl,
-                                &result, &pivot_out, &pv_stage, &scratch, &pv, &tmp};
+                                &result, &pivot_out, &pv_stage, &scratch, &pv, &tmp, &sm_work};
     uint64_t t = 0;
     for (auto* b : bufs) t += b->bytes;
     return t;
@@ -212,7 +213,7 @@ kc_status kc_graph_create(const uint32_t* row_ptr, const uint32_t* col_idx, uint
 kc_status kc_graph_destroy(kc_graph* g) {
     if (!g) return KC_OK;
     DevBuf* bufs[] = {&g->row_ptr, &g->col, &g->new_of_old, &g->old_of_new, &g->core, &g->roots, &g->ctl,
-                       &g->result, &g->pivot_out, &g->pv_stage, &g->scratch, &g->pv, &g->tmp};
+                       &g->result, &g->pivot_out, &g->pv_stage, &g->scratch, &g->pv, &g->tmp, &g->sm_work};
     for (auto* b : bufs) dev_free(*b);
     delete g;
     return KC_OK;
@@ -246,6 +247,20 @@ kc_status kc_graph_last_work(const kc_graph* g, uint64_t* units) {
     return KC_OK;
 }
 
+kc_status kc_graph_last_sm_work(const kc_graph* g, uint64_t* per_sm, uint32_t cap, uint32_t* slots_out) {
+    clear_error();
+    if (!g || !slots_out) return set_error(KC_E_INVALID_ARG, "NULL argument");
+    if (cap && !per_sm) return set_error(KC_E_INVALID_ARG, "per_sm is NULL");
+    std::vector<uint64_t> w(SM_WORK_SLOTS, 0);
+    if (g->sm_work.ptr) KC_CUDA(cudaMemcpy(w.data(), g->sm_work.ptr, SM_WORK_SLOTS * 8, cudaMemcpyDeviceToHost));
+    uint32_t slots = (uint32_t)std::max(g->sm_count, 0);
+    for (uint32_t i = 0; i < SM_WORK_SLOTS; ++i)
+        if (w[i]) slots = std::max(slots, i + 1);
+    for (uint32_t i = 0; i < cap; ++i) per_sm[i] = i < SM_WORK_SLOTS ? w[i] : 0;
+    *slots_out = slots;
+    return KC_OK;
+}
+
 kc_status kc_graph_export(const kc_graph* g, uint32_t* dag_row_ptr, uint32_t* dag_col, uint32_t* new_of_old,
                           uint32_t* core) {
     clear_error();
@@ -270,7 +285,8 @@ static kc_status resolve(const kc_graph* g, uint32_t k, int pivot, int scheme, u
     if (!g) return set_error(KC_E_INVALID_ARG, "NULL graph");
     if (k == 0) return set_error(KC_E_INVALID_ARG, "k must be >= 1");
     if (pivot != 0 && pivot != 1) return set_error(KC_E_INVALID_ARG, "pivot must be 0 or 1");
-    if (scheme != KC_SCHEME_AUTO && scheme != KC_SCHEME_VC && scheme != KC_SCHEME_EC)
+    if (scheme != KC_SCHEME_AUTO && scheme != KC_SCHEME_VC && scheme != KC_SCHEME_EC && scheme != KC_SCHEME_VC_LIST &&
+        scheme != KC_SCHEME_EC_LIST)
         return set_error(KC_E_INVALID_ARG, "unknown scheme %d", scheme);
     if (subwarp != 0 && subwarp != 1 && subwarp != 2 && subwarp != 4 && subwarp != 8 && subwarp != 16 && subwarp != 32)
         return set_error(KC_E_INVALID_ARG, "subwarp must be 0, 1, 2, 4, 8, 16 or 32");
@@ -289,6 +305,8 @@ static kc_status resolve(const kc_graph* g, uint32_t k, int pivot, int scheme, u
     return KC_OK;
 }
 
+static bool list_scheme(int scheme) { return scheme == KC_SCHEME_VC_LIST || scheme == KC_SCHEME_EC_LIST; }
+
 kc_status kc_count_async(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_t subwarp, kc_result* result_dev,
                          uint64_t* per_vertex_dev, void* stream) {
     clear_error();
@@ -297,6 +315,8 @@ kc_status kc_count_async(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_
     if (!result_dev) return set_error(KC_E_INVALID_ARG, "result_dev is NULL");
     if (per_vertex_dev && !is_device_pointer(per_vertex_dev))
         return set_error(KC_E_INVALID_ARG, "per_vertex_dev must be device memory");
+    if (!pivot && per_vertex_dev && list_scheme(a.scheme))
+        return set_error(KC_E_UNSUPPORTED, "the list traversal gives totals only");
     // per-vertex counts: from the traversal the call names, except for
     // k <= 2 (closed forms in the pivoting path) and sizes the orientation
     // traversal does not take
@@ -317,6 +337,8 @@ static kc_status count_sync(kc_graph* g, uint32_t k, int pivot, int scheme, uint
     if (!lo_out) return set_error(KC_E_INVALID_ARG, "total_out is NULL");
     CountArgs a;
     KC_CHECK(resolve(g, k, pivot, scheme, subwarp, a));
+    if (!pivot && per_vertex_out && list_scheme(a.scheme))
+        return set_error(KC_E_UNSUPPORTED, "the list traversal gives totals only");
     // per-vertex counts: as in kc_count_async
     if (per_vertex_out && !orient_per_vertex(g, k)) pivot = 1;
     cudaStream_t s = (cudaStream_t)stream;

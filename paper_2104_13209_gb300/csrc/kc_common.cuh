@@ -100,6 +100,7 @@ struct kc_graph {
     kc::DevBuf scratch;      // per-block scratch (global-memory bitmaps and stacks)
     kc::DevBuf pv;           // u64 per-vertex accumulators (library numbering) + overflow words
     kc::DevBuf tmp;          // misc temporaries
+    kc::DevBuf sm_work;      // u64[SM_WORK_SLOTS]: work units per SM of the last orientation-mode count
     uint64_t device_bytes() const;
 };
 
@@ -124,10 +125,24 @@ kc_status sort_ids_by_key(const uint32_t* key, uint32_t n, uint32_t max_key, uin
 // kc_orient.cu
 kc_status build_graph(kc_graph* g, const uint32_t* d_rp, const uint32_t* d_ci, int validate, cudaStream_t s);
 
+// Work units per SM of an orientation-mode count (Fig. 7's load balance):
+// slots indexed by %smid.
+static constexpr uint32_t SM_WORK_SLOTS = 1024;
+
+// kc_list.cu: the orientation traversal on sorted vertex lists instead of
+// binary-encoded sub-graphs (the paper's comparison point), 3 <= k <=
+// LIST_MAX_K.  list_launch enqueues its kernel (ctl zeroed and its deadline
+// set by the caller, cursor a zeroed counter, sm_work nullable); the caller
+// finalises the result.  list_scratch_words: global scratch it takes.
+static constexpr uint32_t LIST_MAX_K = 16;
+kc_status list_launch(kc_graph* g, uint32_t k, bool ec, Ctl* ctl, unsigned* cursor, unsigned long long* sm_work,
+                      cudaStream_t s);
+size_t list_scratch_words(const kc_graph* g, uint32_t k);
+
 // kc_count.cu
 struct CountArgs {
     uint32_t k;
-    int scheme;       // KC_SCHEME_VC / EC (resolved)
+    int scheme;       // KC_SCHEME_VC / EC / VC_LIST / EC_LIST (resolved)
     uint32_t subwarp; // resolved group width
     int pivot;
     uint64_t* per_vertex_dev;  // input numbering, may be null
@@ -228,6 +243,12 @@ namespace kc {
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned r;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned smid() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
     return r;
 }
 

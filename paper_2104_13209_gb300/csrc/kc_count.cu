@@ -503,6 +503,10 @@ __global__ void __launch_bounds__(BLOCK) k_count_orient(const CountParams P) {
         add_u128(&P.ctl->total_lo, &P.ctl->total_hi, lo);
         if (hi) atomicAdd(&P.ctl->total_hi, hi);
         atomicAdd(&P.ctl->words, words);
+        if (P.sm_work) {
+            const unsigned sm = smid();
+            if (sm < SM_WORK_SLOTS) atomicAdd(&P.sm_work[sm], words);
+        }
     }
 }
 
@@ -626,7 +630,9 @@ kc_status count_reserve(kc_graph* g, uint32_t k_max, int pivot, int per_vertex, 
     (void)s;
     if (per_vertex) KC_CHECK(dev_alloc(g->pv, ((size_t)g->n + 16) * 8));
     KC_CHECK(dev_alloc(g->ctl, ctl_bytes()));
+    KC_CHECK(dev_alloc(g->sm_work, SM_WORK_SLOTS * 8));
     size_t need = 64;
+    for (uint32_t k = 3; k <= std::min<uint32_t>(k_max, LIST_MAX_K); ++k) need = std::max(need, list_scratch_words(g, k) + 64);
     for (uint32_t G : {1u, 2u, 4u, 8u, 16u, 32u})
         for (int ec = 0; ec < 2; ++ec)
             for (uint32_t k = 3; k <= std::min<uint32_t>(k_max, MAX_DEPTH + 4); ++k) {
@@ -652,6 +658,9 @@ kc_status count_launch(kc_graph* g, const CountArgs& a, kc_result* result_dev, c
     KC_CHECK(dev_alloc(g->ctl, ctl_bytes()));
     Ctl* ctl = (Ctl*)g->ctl.ptr;
     KC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl) + sizeof(WorkCtl), s));
+    KC_CHECK(dev_alloc(g->sm_work, SM_WORK_SLOTS * 8));
+    unsigned long long* sm_work = (unsigned long long*)g->sm_work.ptr;
+    KC_CUDA(cudaMemsetAsync(sm_work, 0, SM_WORK_SLOTS * 8, s));
     if (k <= 2 || (uint64_t)k > (uint64_t)g->d_max + 1) {
         unsigned long long v = k == 1 ? g->n : (k == 2 ? g->m : 0ull);
         k_write_result<<<1, 1, 0, s>>>(result_dev, v);
@@ -662,11 +671,24 @@ kc_status count_launch(kc_graph* g, const CountArgs& a, kc_result* result_dev, c
     if (k > MAX_DEPTH + 4)
         return set_error(KC_E_UNSUPPORTED, "orientation traversal supports k <= %d; use pivoting for larger k",
                          MAX_DEPTH + 4);
+    unsigned long long budget = g->time_limit_s > 0 ? (unsigned long long)(g->time_limit_s * 1e9) : 0ull;
+    if (a.scheme == KC_SCHEME_VC_LIST || a.scheme == KC_SCHEME_EC_LIST) {
+        // the traversal on sorted lists (no binary encoding)
+        if (a.per_vertex_dev) return set_error(KC_E_UNSUPPORTED, "the list traversal gives totals only");
+        k_set_deadline<<<1, 1, 0, s>>>(ctl, budget);
+        note_launch();
+        KC_CUDA(cudaGetLastError());
+        WorkCtl* wc = reinterpret_cast<WorkCtl*>(ctl + 1);
+        KC_CHECK(list_launch(g, k, a.scheme == KC_SCHEME_EC_LIST, ctl, &wc->root_cursor, sm_work, s));
+        k_finalize<<<1, 1, 0, s>>>(ctl, result_dev);
+        note_launch();
+        KC_CUDA(cudaGetLastError());
+        return KC_OK;
+    }
     const bool ec = a.scheme == KC_SCHEME_EC;
     const uint32_t G = a.subwarp;
     const uint64_t n_work = roots_with_outdeg_at_least(g, k - 1);
     const uint64_t n_big = roots_with_outdeg_at_least(g, std::max<uint64_t>(SMALL_D + 1, k - 1));
-    unsigned long long budget = g->time_limit_s > 0 ? (unsigned long long)(g->time_limit_s * 1e9) : 0ull;
     const bool pv = a.per_vertex_dev != nullptr;
     if (pv && !deep_supported(g, k, true))
         return set_error(KC_E_UNSUPPORTED, "per-vertex counts in orientation mode need 3 <= k <= 36");
@@ -725,6 +747,7 @@ kc_status count_launch(kc_graph* g, const CountArgs& a, kc_result* result_dev, c
     P.gscratch_words = geo.gscratch_words;
     P.hash_words = geo.hash_words;
     P.ctl = ctl;
+    P.sm_work = sm_work;
     if (n_big) KC_CUDA(cudaMemsetAsync(g->tmp.ptr, 0, (size_t)n_big * 4, s));
     k_set_deadline<<<1, 1, 0, s>>>(ctl, budget);
     note_launch();

@@ -1285,6 +1285,10 @@ __global__ void __launch_bounds__(DBLOCK) k_count_deep(const DeepParams D) {
         add_u128(&P.ctl->total_lo, &P.ctl->total_hi, lo);
         if (hi) atomicAdd(&P.ctl->total_hi, hi);
         atomicAdd(&P.ctl->words, words);
+        if (P.sm_work) {
+            const unsigned sm = smid();
+            if (sm < SM_WORK_SLOTS) atomicAdd(&P.sm_work[sm], words);
+        }
     }
 }
 
@@ -1382,6 +1386,7 @@ kc_status deep_launch(kc_graph* g, uint32_t k, bool ec, uint32_t n_big, uint32_t
     P.gscratch_words = geo.gscratch_words;
     P.hash_words = geo.hash_words;
     P.ctl = ctl;
+    P.sm_work = (unsigned long long*)g->sm_work.ptr;
     D.ec = ec;
     D.wp = geo.wp;
     D.wide_levels = geo.wide_levels;

@@ -30,6 +30,7 @@ struct CountParams {
     size_t gscratch_words;
     uint32_t hash_words;       // shared-memory words of the candidate position table (0: binary search)
     Ctl* ctl;
+    unsigned long long* sm_work;  // nullable: work units per SM (SM_WORK_SLOTS entries)
 };
 
 // Extra counters of the kernel (kept right after the Ctl record).

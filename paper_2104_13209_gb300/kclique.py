@@ -33,6 +33,8 @@ KC_ORIENT_DEGENERACY = 1
 KC_SCHEME_AUTO = 0
 KC_SCHEME_VC = 1
 KC_SCHEME_EC = 2
+KC_SCHEME_VC_LIST = 3
+KC_SCHEME_EC_LIST = 4
 
 KC_FLAG_TOTAL_OVERFLOW = 1
 KC_FLAG_VERTEX_OVERFLOW = 2
@@ -41,14 +43,15 @@ KC_FLAG_INTERNAL = 8
 KC_FLAG_TOTAL_OVERFLOW128 = 16
 
 _ORIENT = {"degree": KC_ORIENT_DEGREE, "degeneracy": KC_ORIENT_DEGENERACY}
-_SCHEME = {"auto": KC_SCHEME_AUTO, "vc": KC_SCHEME_VC, "ec": KC_SCHEME_EC}
+_SCHEME = {"auto": KC_SCHEME_AUTO, "vc": KC_SCHEME_VC, "ec": KC_SCHEME_EC, "vc-list": KC_SCHEME_VC_LIST,
+           "ec-list": KC_SCHEME_EC_LIST}
 
 # Every exported symbol of include/kclique.h.
 EXPORTED = [
     "kc_last_error", "kc_status_name", "kc_version", "kc_graph_create", "kc_graph_destroy", "kc_graph_info_get",
     "kc_graph_export", "kc_count", "kc_count128", "kc_count_async", "kc_count_noalloc", "kc_graph_reserve", "kc_count_all",
     "kc_count_all128",
-    "kc_graph_set_time_limit", "kc_launch_count", "kc_graph_last_work",
+    "kc_graph_set_time_limit", "kc_launch_count", "kc_graph_last_work", "kc_graph_last_sm_work",
     "kc_batch_create", "kc_batch_destroy", "kc_batch_graph_info", "kc_batch_set_time_limit", "kc_batch_count",
     "kc_batch_tune", "kc_batch_capture", "kc_batch_exec_launch", "kc_batch_exec_destroy",
     "kc_server_create", "kc_server_add_graph", "kc_server_set_time_limit", "kc_server_submit", "kc_server_poll",
@@ -142,6 +145,8 @@ def load(build_if_missing: bool = False):
     lib.kc_graph_set_time_limit.argtypes = [vp, ctypes.c_double]
     lib.kc_graph_last_work.argtypes = [vp, ctypes.POINTER(u64)]
     lib.kc_graph_last_work.restype = i32
+    lib.kc_graph_last_sm_work.argtypes = [vp, vp, u32, ctypes.POINTER(u32)]
+    lib.kc_graph_last_sm_work.restype = i32
     lib.kc_batch_create.argtypes = [vp, vp, u32, u64, vp, u32, i32, i32, i32, vp, ctypes.POINTER(vp)]
     lib.kc_batch_destroy.argtypes = [vp]
     lib.kc_batch_graph_info.argtypes = [vp, u32, ctypes.POINTER(u32), ctypes.POINTER(u64), ctypes.POINTER(u32)]
@@ -280,6 +285,15 @@ class Graph:
 
     def set_time_limit(self, seconds: float):
         _check(load().kc_graph_set_time_limit(self._h, float(seconds)))
+
+    def last_sm_work(self) -> np.ndarray:
+        """Work units per SM of the last orientation-mode count (kc_graph_last_sm_work)."""
+        lib = load()
+        slots = ctypes.c_uint32()
+        _check(lib.kc_graph_last_sm_work(self._h, None, 0, ctypes.byref(slots)))
+        out = np.zeros(max(slots.value, 1), dtype=np.uint64)
+        _check(lib.kc_graph_last_sm_work(self._h, out.ctypes.data, slots.value, ctypes.byref(slots)))
+        return out[: slots.value]
 
     def export(self, core: bool = False):
         """(dag_row_ptr, dag_col, new_of_old, core or None) as numpy arrays."""

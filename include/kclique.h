@@ -233,6 +233,23 @@ kc_status kc_count_noalloc(const kc_graph* g, uint32_t k, int scheme, uint32_t s
  * pivot and per_vertex arguments are accepted for that future use. */
 kc_status kc_graph_reserve(kc_graph* g, uint32_t k_max, int pivot, int per_vertex, void* stream);
 
+/* List the k-cliques (the paper's conclusion names listing as a use of the
+ * same traversal): the orientation traversal on sorted vertex lists
+ * (KC_SCHEME_VC_LIST), where every member of the last intersection closes
+ * one clique and is written out instead of only counted.
+ *   3 <= k <= 16 (KC_E_UNSUPPORTED otherwise, KC_E_INVALID_ARG for k = 0).
+ *   cliques_dev (device memory, cap * k entries, nullable when cap = 0):
+ *     clique i is cliques_dev[i k .. i k + k), k input vertex ids in the
+ *     orientation order (the root first).  Which cliques fill the cap when
+ *     there are more is unspecified, and so is their order.
+ *   count_out (host): the number of k-cliques of the graph, also when it
+ *     exceeds cap (then exactly cap cliques are written).
+ * Synchronises the stream.  The time limit of the graph applies
+ * (KC_E_TIMEOUT; the written cliques are then a subset).  Work units of the
+ * call: membership tests (kc_graph_last_work, kc_graph_last_sm_work). */
+kc_status kc_list_cliques(kc_graph* g, uint32_t k, uint32_t* cliques_dev, uint64_t cap, uint64_t* count_out,
+                          void* stream);
+
 /* Every clique size at once by pivoting (Fig. 3, Section 2.3).
  *   counts (host, cap entries): counts[j] = number of j-cliques modulo 2^64,
  *     counts[0] = 1 by convention, entries beyond the clique number are 0.

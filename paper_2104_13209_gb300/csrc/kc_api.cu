@@ -394,6 +394,29 @@ kc_status kc_count(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_t subw
     return count_sync(g, k, pivot, scheme, subwarp, total_out, &hi, per_vertex_out, flags_out, stream);
 }
 
+kc_status kc_list_cliques(kc_graph* g, uint32_t k, uint32_t* cliques_dev, uint64_t cap, uint64_t* count_out,
+                          void* stream) {
+    clear_error();
+    if (!g || !count_out) return set_error(KC_E_INVALID_ARG, "NULL argument");
+    if (k == 0) return set_error(KC_E_INVALID_ARG, "k must be >= 1");
+    if (k < 3 || k > LIST_MAX_K) return set_error(KC_E_UNSUPPORTED, "listing takes 3 <= k <= %u", LIST_MAX_K);
+    if (cap && !cliques_dev) return set_error(KC_E_INVALID_ARG, "cliques_dev is NULL");
+    if (cap && !is_device_pointer(cliques_dev)) return set_error(KC_E_INVALID_ARG, "cliques_dev must be device memory");
+    if (cap > UINT64_MAX / k) return set_error(KC_E_INVALID_ARG, "cap too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    KC_CHECK(dev_alloc(g->result, sizeof(kc_result) + 64));
+    kc_result* rd = (kc_result*)g->result.ptr;
+    KC_CHECK(list_cliques_launch(g, k, cliques_dev, cap, rd, s));
+    kc_result r;
+    KC_CUDA(cudaMemcpyAsync(&r, rd, sizeof(r), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    g->last_work = r.words;
+    *count_out = r.total;
+    if (r.status != KC_OK) return set_error((kc_status)r.status, "device reported %s", kc_status_name(r.status));
+    if (r.total_hi) return set_error(KC_E_OVERFLOW, "more than 2^64 - 1 cliques");
+    return KC_OK;
+}
+
 static kc_status count_all_common(kc_graph* g, uint64_t* counts_lo, uint64_t* counts_hi, uint8_t* overflow64,
                                   uint8_t* overflow128, uint32_t cap, uint32_t* omega_out, uint32_t per_vertex_k,
                                   uint64_t* per_vertex_out, void* stream) {

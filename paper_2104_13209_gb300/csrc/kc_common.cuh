@@ -133,10 +133,18 @@ static constexpr uint32_t SM_WORK_SLOTS = 1024;
 // binary-encoded sub-graphs (the paper's comparison point), 3 <= k <=
 // LIST_MAX_K.  list_launch enqueues its kernel (ctl zeroed and its deadline
 // set by the caller, cursor a zeroed counter, sm_work nullable); the caller
-// finalises the result.  list_scratch_words: global scratch it takes.
+// finalises the result.  With emitted (a zeroed counter) not null it lists
+// the cliques too: the first cap of them to out (k ids each, input
+// numbering; out may be null when cap is 0).  list_scratch_words: global
+// scratch it takes.
 static constexpr uint32_t LIST_MAX_K = 16;
 kc_status list_launch(kc_graph* g, uint32_t k, bool ec, Ctl* ctl, unsigned* cursor, unsigned long long* sm_work,
-                      cudaStream_t s);
+                      cudaStream_t s, uint32_t* out = nullptr, unsigned long long cap = 0,
+                      unsigned long long* emitted = nullptr);
+// kc_count.cu: listing of the k-cliques (3 <= k <= LIST_MAX_K) by the list
+// traversal; result (count, flags, status) to result_dev.
+kc_status list_cliques_launch(kc_graph* g, uint32_t k, uint32_t* out, uint64_t cap, kc_result* result_dev,
+                              cudaStream_t s);
 size_t list_scratch_words(const kc_graph* g, uint32_t k);
 
 // kc_count.cu

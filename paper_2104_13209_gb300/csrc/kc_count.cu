@@ -764,6 +764,30 @@ kc_status count_launch(kc_graph* g, const CountArgs& a, kc_result* result_dev, c
 }
 
 
+kc_status list_cliques_launch(kc_graph* g, uint32_t k, uint32_t* out, uint64_t cap, kc_result* result_dev,
+                              cudaStream_t s) {
+    if (k < 3 || k > LIST_MAX_K) return set_error(KC_E_UNSUPPORTED, "listing takes 3 <= k <= %u", LIST_MAX_K);
+    KC_CHECK(dev_alloc(g->ctl, ctl_bytes()));
+    Ctl* ctl = (Ctl*)g->ctl.ptr;
+    WorkCtl* wc = reinterpret_cast<WorkCtl*>(ctl + 1);
+    // the cliques-found counter sits right after the work counters
+    unsigned long long* emitted = reinterpret_cast<unsigned long long*>(wc + 1);
+    KC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl) + sizeof(WorkCtl) + sizeof(unsigned long long), s));
+    KC_CHECK(dev_alloc(g->sm_work, SM_WORK_SLOTS * 8));
+    unsigned long long* sm_work = (unsigned long long*)g->sm_work.ptr;
+    KC_CUDA(cudaMemsetAsync(sm_work, 0, SM_WORK_SLOTS * 8, s));
+    const unsigned long long budget = g->time_limit_s > 0 ? (unsigned long long)(g->time_limit_s * 1e9) : 0ull;
+    k_set_deadline<<<1, 1, 0, s>>>(ctl, budget);
+    note_launch();
+    KC_CUDA(cudaGetLastError());
+    if ((uint64_t)k <= (uint64_t)g->d_max + 1)
+        KC_CHECK(list_launch(g, k, false, ctl, &wc->root_cursor, sm_work, s, out, cap, emitted));
+    k_finalize<<<1, 1, 0, s>>>(ctl, result_dev);
+    note_launch();
+    KC_CUDA(cudaGetLastError());
+    return KC_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Batched counts: many (graph, k) queries in one persistent launch.  The
 // item space is every query's roots with out-degree >= k - 1: first the big

@@ -27,10 +27,16 @@ struct ListParams {
     uint32_t n_items;               // VC: roots with out-degree >= k - 1; EC: DAG edges
     int ec;
     uint32_t dcap;                  // entries per stack level (the largest out-degree)
-    uint32_t* lists;                // per warp: (k - 2) levels of dcap entries
+    uint32_t* lists;                // per warp: max(k - 3, 1) levels of dcap entries
     unsigned* cursor;               // next unclaimed item (zeroed before the launch)
     unsigned long long* sm_work;    // nullable: work units per SM (SM_WORK_SLOTS entries)
     Ctl* ctl;
+    // listing (the EMIT kernel only): clique i goes to out[i k .. i k + k)
+    // in the input numbering, for i < cap; emitted counts every clique found
+    uint32_t* out;
+    unsigned long long cap;
+    unsigned long long* emitted;
+    const uint32_t* old_of_new;
 };
 
 // Source vertex of DAG edge e: the largest v with rp[v] <= e (one thread).
@@ -77,6 +83,41 @@ __device__ __forceinline__ uint32_t list_intersect(const uint32_t* L, uint32_t f
     return cnt;
 }
 
+// Listing form of the last intersection: every member x of L[from, to)
+// that is an out-neighbour of u closes the clique path + {x} (path: plen
+// vertices, the same in every lane).  The warp reserves the slots of each
+// 32 members with one atomic; a clique whose slot is at or beyond P.cap is
+// counted but not written.  Returns the number of cliques closed.
+__device__ uint32_t list_emit(const ListParams& P, const uint32_t* L, uint32_t from, uint32_t to, uint32_t u,
+                              const uint32_t* path, uint32_t plen, int lane) {
+    const uint32_t b = __ldg(P.rp + u), e = __ldg(P.rp + u + 1);
+    uint32_t cnt = 0;
+    for (uint32_t base = from; base < to; base += 32) {
+        const uint32_t i = base + (uint32_t)lane;
+        bool hit = false;
+        uint32_t x = 0;
+        if (i < to) {
+            x = L[i];
+            hit = row_has(P.col, b, e, x);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (bal == 0) continue;
+        unsigned long long first = 0;
+        if (lane == 0) first = atomicAdd(P.emitted, (unsigned long long)__popc(bal));
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (hit) {
+            const unsigned long long slot = first + (unsigned long long)__popc(bal & lanemask_lt());
+            if (slot < P.cap) {
+                uint32_t* o = P.out + slot * P.k;
+                for (uint32_t t = 0; t < plen; ++t) o[t] = __ldg(P.old_of_new + path[t]);
+                o[plen] = __ldg(P.old_of_new + x);
+            }
+        }
+        cnt += __popc(bal);
+    }
+    return cnt;
+}
+
 // One work item by one warp: the subtree of root v below its level-0
 // candidates j_first .. j_end - 1 (VC: all of N+(v); EC: the one root edge
 // v -> N+(v)[j_first]).  Levels are sorted lists: level 0 is v's DAG row,
@@ -85,6 +126,7 @@ __device__ __forceinline__ uint32_t list_intersect(const uint32_t* L, uint32_t f
 // the intersection are counted instead of stored.  stk: this warp's lists,
 // (k - 3) levels of dcap entries.  Counts go to acc (the same in every
 // lane), membership tests to work; stop is set when the time limit passed.
+template <bool EMIT>
 __device__ void list_walk(const ListParams& P, uint32_t v, uint32_t j_first, uint32_t j_end, uint32_t* stk,
                           Acc& acc, unsigned long long& work, int lane, bool& stop) {
     const uint32_t b0 = __ldg(P.rp + v);
@@ -118,7 +160,16 @@ __device__ void list_walk(const ListParams& P, uint32_t v, uint32_t j_first, uin
         J[l] = from;
         work += to - from;
         if (R == 2) {  // u and one more: every common member closes a clique
-            acc.add(list_intersect(L, from, to, P.rp, P.col, u, nullptr, lane));
+            if (EMIT) {
+                // the clique's other vertices: the root and the vertex chosen at
+                // each level (the one just before that level's cursor)
+                uint32_t path[LIST_MAX_K];
+                path[0] = v;
+                for (int t = 0; t <= l; ++t) path[1 + t] = Lv[t][J[t] - 1];
+                acc.add(list_emit(P, L, from, to, u, path, (uint32_t)l + 2, lane));
+            } else {
+                acc.add(list_intersect(L, from, to, P.rp, P.col, u, nullptr, lane));
+            }
             continue;
         }
         uint32_t* out = stk + (size_t)l * P.dcap;
@@ -135,6 +186,7 @@ __device__ void list_walk(const ListParams& P, uint32_t v, uint32_t j_first, uin
 
 // Persistent warps claim work items from a global cursor: roots (VC, in
 // decreasing out-degree) or DAG edges (EC).
+template <bool EMIT>
 __global__ void __launch_bounds__(LBLOCK) k_count_list(const ListParams P) {
     const int lane = threadIdx.x & 31;
     const uint32_t gw = blockIdx.x * LWARPS + (threadIdx.x >> 5);
@@ -160,7 +212,7 @@ __global__ void __launch_bounds__(LBLOCK) k_count_list(const ListParams P) {
             j0 = 0;
             j1 = NONE;
         }
-        list_walk(P, v, j0, j1, stk, acc, work, lane, stop);
+        list_walk<EMIT>(P, v, j0, j1, stk, acc, work, lane, stop);
     }
     // every lane holds the same totals: lane 0 publishes them
     if (lane == 0) {
@@ -179,7 +231,7 @@ __global__ void __launch_bounds__(LBLOCK) k_count_list(const ListParams P) {
 // ---------------------------------------------------------------------------
 static kc_status list_geometry(const kc_graph* g, uint32_t k, int* blocks, size_t* words) {
     int bps = 0;
-    KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_count_list, LBLOCK, 0));
+    KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_count_list<true>, LBLOCK, 0));
     if (bps < 1) return set_error(KC_E_UNSUPPORTED, "list traversal kernel cannot be resident");
     *blocks = bps * g->sm_count;
     const size_t nl = k > 3 ? k - 3 : 1;
@@ -195,7 +247,7 @@ size_t list_scratch_words(const kc_graph* g, uint32_t k) {
 }
 
 kc_status list_launch(kc_graph* g, uint32_t k, bool ec, Ctl* ctl, unsigned* cursor, unsigned long long* sm_work,
-                      cudaStream_t s) {
+                      cudaStream_t s, uint32_t* out, unsigned long long cap, unsigned long long* emitted) {
     if (k < 3 || k > LIST_MAX_K)
         return set_error(KC_E_UNSUPPORTED, "the list traversal takes 3 <= k <= %u", LIST_MAX_K);
     int blocks = 0;
@@ -227,7 +279,15 @@ kc_status list_launch(kc_graph* g, uint32_t k, bool ec, Ctl* ctl, unsigned* curs
     P.cursor = cursor;
     P.sm_work = sm_work;
     P.ctl = ctl;
-    k_count_list<<<blocks, LBLOCK, 0, s>>>(P);
+    if (emitted) {
+        P.out = out;
+        P.cap = out ? cap : 0ull;
+        P.emitted = emitted;
+        P.old_of_new = (const uint32_t*)g->old_of_new.ptr;
+        k_count_list<true><<<blocks, LBLOCK, 0, s>>>(P);
+    } else {
+        k_count_list<false><<<blocks, LBLOCK, 0, s>>>(P);
+    }
     note_launch();
     KC_CUDA(cudaGetLastError());
     return KC_OK;

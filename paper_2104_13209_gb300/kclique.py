@@ -51,7 +51,7 @@ EXPORTED = [
     "kc_last_error", "kc_status_name", "kc_version", "kc_graph_create", "kc_graph_destroy", "kc_graph_info_get",
     "kc_graph_export", "kc_count", "kc_count128", "kc_count_async", "kc_count_noalloc", "kc_graph_reserve", "kc_count_all",
     "kc_count_all128",
-    "kc_graph_set_time_limit", "kc_launch_count", "kc_graph_last_work", "kc_graph_last_sm_work",
+    "kc_graph_set_time_limit", "kc_launch_count", "kc_graph_last_work", "kc_graph_last_sm_work", "kc_list_cliques",
     "kc_batch_create", "kc_batch_destroy", "kc_batch_graph_info", "kc_batch_set_time_limit", "kc_batch_count",
     "kc_batch_tune", "kc_batch_capture", "kc_batch_exec_launch", "kc_batch_exec_destroy",
     "kc_server_create", "kc_server_add_graph", "kc_server_set_time_limit", "kc_server_submit", "kc_server_poll",
@@ -147,6 +147,8 @@ def load(build_if_missing: bool = False):
     lib.kc_graph_last_work.restype = i32
     lib.kc_graph_last_sm_work.argtypes = [vp, vp, u32, ctypes.POINTER(u32)]
     lib.kc_graph_last_sm_work.restype = i32
+    lib.kc_list_cliques.argtypes = [vp, u32, vp, u64, ctypes.POINTER(u64), vp]
+    lib.kc_list_cliques.restype = i32
     lib.kc_batch_create.argtypes = [vp, vp, u32, u64, vp, u32, i32, i32, i32, vp, ctypes.POINTER(vp)]
     lib.kc_batch_destroy.argtypes = [vp]
     lib.kc_batch_graph_info.argtypes = [vp, u32, ctypes.POINTER(u32), ctypes.POINTER(u64), ctypes.POINTER(u32)]
@@ -285,6 +287,22 @@ class Graph:
 
     def set_time_limit(self, seconds: float):
         _check(load().kc_graph_set_time_limit(self._h, float(seconds)))
+
+    def list_cliques(self, k: int, cap: int | None = None, stream=None):
+        """(number of k-cliques, uint32 array [min(count, cap), k] of input vertex ids) via kc_list_cliques;
+        cap defaults to the count (one counting call first)."""
+        import torch
+
+        lib = load()
+        if cap is None:
+            cap = self.count(k, scheme="vc-list", stream=stream).total
+        buf = torch.empty(max(cap * k, 1), dtype=torch.int32, device="cuda")
+        cnt = ctypes.c_uint64()
+        _check(lib.kc_list_cliques(self._h, k, buf.data_ptr() if cap else None, cap, ctypes.byref(cnt),
+                                   _stream_ptr(stream)))
+        rows = min(cnt.value, cap)
+        out = buf[: rows * k].cpu().numpy().view(np.uint32).reshape(rows, k)
+        return cnt.value, out
 
     def last_sm_work(self) -> np.ndarray:
         """Work units per SM of the last orientation-mode count (kc_graph_last_sm_work)."""

@@ -1,37 +1,20 @@
 """k-clique listing (kc_list_cliques): the list traversal writes out every
-clique it closes.  The listed sets are compared with a brute-force
-enumeration on small graphs (every k-subset that is a clique, found by
-extending cliques one vertex at a time over increasing ids), their number
-with the oracle's count, and a truncated listing with the full count."""
+clique it closes.  The listed sets are compared with the reference listing
+of tests/clique_listing_ref.py (pinned on the CPU by
+tests/test_listing_ref.py), their number with the oracle's count, and a
+truncated listing with the full count."""
 import itertools
 import math
 
 import pytest
 
 from oracle import oracle as O
+from tests.clique_listing_ref import brute_force_cliques
 from tests.gpu_common import graph, kclique, synth
 
 pytestmark = pytest.mark.gpu
 
 pytest.importorskip("torch")
-
-
-def brute_force_cliques(g, k):
-    """Every k-clique of g as a sorted tuple: each clique is reached once,
-    by adding its vertices in increasing id order."""
-    adj = [set(g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]].tolist()) for v in range(g.n)]
-    out = []
-
-    def extend(clique, cand):
-        if len(clique) == k:
-            out.append(tuple(clique))
-            return
-        for x in sorted(cand):
-            extend(clique + [x], {y for y in cand if y > x} & adj[x])
-
-    for v in range(g.n):
-        extend([v], {y for y in adj[v] if y > v})
-    return set(out)
 
 
 def listed_set(rows):

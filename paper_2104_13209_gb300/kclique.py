@@ -290,12 +290,12 @@ class Graph:
 
     def list_cliques(self, k: int, cap: int | None = None, stream=None):
         """(number of k-cliques, uint32 array [min(count, cap), k] of input vertex ids) via kc_list_cliques;
-        cap defaults to the count (one counting call first)."""
+        cap defaults to the count (one counting call by the bitmap traversal first)."""
         import torch
 
         lib = load()
         if cap is None:
-            cap = self.count(k, scheme="vc-list", stream=stream).total
+            cap = self.count(k, stream=stream).total
         buf = torch.empty(max(cap * k, 1), dtype=torch.int32, device="cuda")
         cnt = ctypes.c_uint64()
         _check(lib.kc_list_cliques(self._h, k, buf.data_ptr() if cap else None, cap, ctypes.byref(cnt),

@@ -6,7 +6,10 @@
 // not extract a binary-encoded induced sub-graph intersect.  One warp per
 // work item: a root vertex (vertex-centric) or a root edge (edge-centric,
 // Section 3.2).  The work units are the membership tests; they are also
-// added per SM, for the load-balance measurement of Fig. 7.
+// added per SM, for the load-balance measurement of Fig. 7.  The same walk
+// lists the cliques (the listing the paper's conclusion names as a use of
+// the traversal): in its EMIT form every member of a last intersection is
+// written out with the vertices on its path.
 #include <algorithm>
 #include <cstring>
 

@@ -120,15 +120,17 @@ def test_rmat20_full_size_k4():
         G.close()
 
 
-def test_rmat16_deep_k_golden():
-    """R-MAT scale 16 (edge factor 16; 219 candidates at most under degeneracy
-    order, so the deep traversal's wide levels and its re-encoded nodes both
-    run) at the deep sizes the R-MAT-20 configuration asks for, k = 5, 6 and
-    7: both schemes, both orientations, against the oracle's totals stored by
+@pytest.mark.parametrize("scale", [16, 17])
+def test_rmat_deep_k_golden(scale):
+    """R-MAT scales 16 and 17 (edge factor 16; at most 219 and 286 candidates
+    under degeneracy order, so the deep traversal's wide levels and its
+    re-encoded nodes both run) at the deep sizes the R-MAT-20 configuration
+    asks for (k = 5, 6 and, where stored, 7): both schemes, both
+    orientations, against the oracle's totals stored by
     tests/golden/make_golden.py."""
     with open(os.path.join(GOLDEN, "counts.json")) as f:
-        rec = json.load(f)["rmat16_ef16_s0"]
-    g = synth.rmat(16, 16, seed=0)
+        rec = json.load(f)[f"rmat{scale}_ef16_s0"]
+    g = synth.rmat(scale, 16, seed=0)
     assert g.num_edges == rec["num_edges"]
     for orient in ("degeneracy", "degree"):
         G = graph(g, orient)

@@ -138,9 +138,11 @@ kc_status kc_graph_info_get(const kc_graph* g, kc_graph_info* out);
 kc_status kc_graph_set_time_limit(kc_graph* g, double seconds);
 
 /* Work units of the last synchronous count on this graph (kc_count,
- * kc_count128, kc_count_all): for the graph-orientation traversal the 32-bit
- * bitmap words intersected (one AND plus one popcount each); for pivoting the
- * search-tree nodes analysed (a pivot search each). */
+ * kc_count128, kc_count_all, kc_list_cliques): for the graph-orientation
+ * traversal the 32-bit bitmap words intersected (one AND plus one popcount
+ * each), for the list traversal (KC_SCHEME_VC_LIST / EC_LIST and listing) the
+ * membership tests, for pivoting the search-tree nodes analysed (a pivot
+ * search each). */
 kc_status kc_graph_last_work(const kc_graph* g, uint64_t* units);
 
 /* The same work units of the last orientation-mode count on this graph
@@ -197,7 +199,7 @@ kc_status kc_count128(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_t s
  * working memory is taken from the handle; call kc_graph_reserve first if the
  * call will be captured into a CUDA graph (no allocation happens then).
  * per_vertex_dev: nullable, n entries of device memory, input numbering
- * (computed by the pivoting traversal, as in kc_count). */
+ * (from the traversal kc_count would use for the same arguments). */
 kc_status kc_count_async(kc_graph* g, uint32_t k, int pivot, int scheme, uint32_t subwarp, kc_result* result_dev,
                          uint64_t* per_vertex_dev, void* stream);
 

@@ -96,7 +96,8 @@ typedef struct kc_result {
     uint64_t total_hi;     /* high 64 bits (non-zero iff the count overflowed uint64) */
     uint32_t flags;        /* KC_FLAG_* */
     uint32_t status;       /* KC_OK or the kc_status of a device-side failure */
-    uint64_t words;        /* work units: bitmap words intersected (orientation) or tree nodes (pivoting) */
+    uint64_t words;        /* work units: bitmap words intersected (orientation), membership tests
+                              (list traversal) or tree nodes (pivoting) */
 } kc_result;
 
 /* ---- errors -------------------------------------------------------------- */

@@ -125,7 +125,7 @@ def test_rmat_deep_k_golden(scale):
     """R-MAT scales 16 and 17 (edge factor 16; at most 219 and 286 candidates
     under degeneracy order, so the deep traversal's wide levels and its
     re-encoded nodes both run) at the deep sizes the R-MAT-20 configuration
-    asks for (k = 5, 6 and, where stored, 7): both schemes, both
+    asks for (k = 5, 6 and 7): both schemes, both
     orientations, against the oracle's totals stored by
     tests/golden/make_golden.py."""
     with open(os.path.join(GOLDEN, "counts.json")) as f:
